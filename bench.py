@@ -1,0 +1,433 @@
+#!/usr/bin/env python
+"""Benchmark of the stream-compaction hot path on GB300.
+
+Default workload (one "step"): the fused single-pass compaction of N = 2^28
+uniform uint32 entries, keep x < t, at selectivities 1 %, 50 % and 99 % (three
+launches over the same 1 GiB input, which is larger than L2, so no flush is
+needed between steps). Prints one JSON line.
+
+  value      compacted input elements per second over all ranks (device time,
+             CUDA events on the launching stream, max over ranks)
+  roofline   the fused kernel's algorithmic bytes (4 N + 4 K per launch) over
+             its average launch time, against the measured HBM copy bandwidth
+  e2e        the same metric through the C ABI with host buffers: the step's
+             input uploaded from pinned memory, its results read back
+  cpu_baseline  the CPU oracle (plain sequential loop) on the host cores
+
+--impl reference times the CPU oracle as the reference arm on the same
+workload (bounded samples per step). Multi-GPU: replicas (each rank runs the
+whole workload on its own GPU; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "compacted elements/s and % of HBM peak; batched p50/p99 latency vs plain launches"
+N_LARGE = 1 << 28
+SELECTIVITIES = (0.01, 0.5, 0.99)
+SEED = 2
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1709_07781_gb300", "csrc", f)
+                  for f in ("k_compact.cu", "ka_dev.cuh")]
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extras", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Dist:
+    def __init__(self, world, rank, local, backend="nccl"):
+        import torch
+        self.world, self.rank, self.local = world, rank, local
+        self.torch = torch
+        self.pg = False
+        if world > 1:
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group(backend=backend, rank=rank, world_size=world)
+            self.dist = dist
+            self.pg = True
+
+    def barrier(self):
+        if self.pg:
+            self.dist.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        t = self.torch.tensor([v], dtype=self.torch.float64,
+                              device="cuda" if self.torch.cuda.is_available() else "cpu")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.dist.destroy_process_group()
+
+
+def aggregate(per_rank_units: float, world: int, max_seconds: float) -> float:
+    """Whole-job throughput: units processed by all ranks over the slowest rank's time."""
+    return per_rank_units * world / max_seconds
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="ka_clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """Per-launch DRAM bytes of the fused kernel from the committed ncu summary,
+    only if it was taken on the current kernel source."""
+    try:
+        with open(PROFILE_TRAFFIC) as fh:
+            d = json.load(fh)
+        entry = d["k_compact_fused"]
+        if entry.get("source_sha") != kernel_source_sha():
+            return None
+        return entry
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    D = Dist(world, rank, local)
+    import paper_1709_07781_gb300 as ka
+    import ka_inputs as ki
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    st = stream.cuda_stream
+    N = N_LARGE
+    thresholds = [ki.threshold_for(s) for s in SELECTIVITIES]
+
+    x = torch.empty(N, dtype=torch.int32, device=dev)
+    out = torch.empty(N, dtype=torch.int32, device=dev)
+    counts = torch.zeros(64, dtype=torch.int32, device=dev)
+    ka.check(ka.ka_generate(x, N, SEED, st))
+    s, ws_bytes = ka.ka_workspace_size(N)
+    ka.check(s)
+    ws_t = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
+    ws = (ws_t.data_ptr() + 255) // 256 * 256
+    ka.check(ka.ka_workspace_init(ws, ws_bytes, st))
+    s, tile = ka.ka_tile_for(ka.KA_KERNEL_COMPACT, N)
+
+    def launch(i):
+        return ka.ka_compact(x, N, None, ka.KA_PRED_LT, thresholds[i], ka.KA_XFORM_NONE, out, counts[i:i + 1],
+                             ws, ws_bytes, None, st)
+
+    for _ in range(max(args.warmup, 3)):
+        for i in range(3):
+            ka.check(launch(i))
+    torch.cuda.synchronize()
+    kept = [int(np.int32(counts[i].item()).view(np.uint32)) for i in range(3)]
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(K)]
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    D.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e_start.record(stream)
+    launches = 0
+    for k in range(K):
+        for i in range(3):
+            ev[k][2 * i].record(stream)
+            launch(i)
+            ev[k][2 * i + 1].record(stream)
+            launches += 1
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    D.barrier()
+    total_ms = e_start.elapsed_time(e_end)
+    per_sel_ms = [sum(ev[k][2 * i].elapsed_time(ev[k][2 * i + 1]) for k in range(K)) / K for i in range(3)]
+    max_total_s = D.max(total_ms / 1000.0)
+    value = aggregate(3.0 * N * K, world, max_total_s)
+
+    peak, peak_kind = measured_peak_gbs()
+    bytes_per_launch = [4.0 * N + 4.0 * kk for kk in kept]
+    avg_launch_s = sum(per_sel_ms) / 3 / 1000.0
+    achieved = (sum(bytes_per_launch) / 3) / avg_launch_s / 1e9
+    traffic = profiled_traffic()
+    roofline = {
+        "kernel": "k_compact_fused<%d,%d>" % tuple(tile),
+        "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+        "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+        "traffic": (traffic["bytes_per_launch_avg"] if traffic else None),
+        "algorithmic_bytes_per_launch": [int(b) for b in bytes_per_launch],
+        "per_selectivity": [{"s": s_, "us": round(ms * 1000, 2), "GB/s": round(b / (ms / 1000) / 1e9, 1),
+                             "frac": round(b / (ms / 1000) / 1e9 / peak, 4)}
+                            for s_, ms, b in zip(SELECTIVITIES, per_sel_ms, bytes_per_launch)],
+    }
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": K,
+        "warmup": max(args.warmup, 3), "ms_per_step": max_total_s * 1000.0 / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "large single compaction: N=2^28 uint32 uniform (SplitMix64 seed 2), keep x < t, "
+                               "t = floor(s 2^32), s = 1%, 50%, 99%; fused single-pass decoupled look-back",
+                   "n": N, "selectivities": list(SELECTIVITIES), "kept": kept, "tile": list(tile),
+                   "l2": "inputs (1 GiB) larger than L2; no flush", "parallelism": "replicas x%d" % world},
+        "roofline": roofline, "gpu_launches": launches, "clocks": clock_info,
+    }
+
+    if not args.no_e2e:
+        result["e2e"] = e2e_large(ka, torch, x, kept, thresholds, ws, ws_bytes, D, min(K, 10))
+    if not args.no_extras:
+        result["extras"] = {"three_launch": three_launch_large(ka, torch, x, thresholds, D, peak)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline_large(kept)
+    D.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def e2e_large(ka, torch, x_dev, kept, thresholds, ws, ws_bytes, D, steps):
+    """Whole step through the C ABI with host buffers: pinned input uploaded,
+    three compactions, counts and kept entries read back."""
+    import numpy as np
+    N = N_LARGE
+    st = torch.cuda.current_stream()
+    h_x = torch.empty(N, dtype=torch.int32, pin_memory=True)
+    h_x.copy_(x_dev.cpu())
+    h_out = [torch.empty(N, dtype=torch.int32, pin_memory=True) for _ in range(3)]
+    h_cnt = torch.zeros(4, dtype=torch.int32, pin_memory=True)
+    d_x = torch.empty_like(x_dev)
+    d_out = [torch.empty_like(x_dev) for _ in range(3)]
+    d_cnt = torch.zeros(4, dtype=torch.int32, device=x_dev.device)
+    h2d = d2h = 0
+
+    def step():
+        nonlocal h2d, d2h
+        d_x.copy_(h_x, non_blocking=True)
+        for i in range(3):
+            ka.check(ka.ka_compact(d_x, N, None, ka.KA_PRED_LT, thresholds[i], 0, d_out[i], d_cnt[i:i + 1], ws,
+                                   ws_bytes, None, st.cuda_stream))
+        h_cnt.copy_(d_cnt, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        for i in range(3):
+            k = int(np.int32(h_cnt[i].item()).view(np.uint32))
+            if k:
+                h_out[i][:k].copy_(d_out[i][:k], non_blocking=True)
+            d2h += 4 * k
+        torch.cuda.current_stream().synchronize()
+        h2d += 4 * N
+        d2h += 16
+
+    step()
+    h2d = d2h = 0
+    D.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    dt = time.perf_counter() - t0
+    D.barrier()
+    dt = D.max(dt)
+    return {"value": aggregate(3.0 * N * steps, D.world, dt), "unit": "elements/s",
+            "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps, "steps": steps,
+            "ms_per_step": dt * 1000.0 / steps}
+
+
+def three_launch_large(ka, torch, x, thresholds, D, peak):
+    """The 3-launch chained version (flag map, exclusive scan, move) at N=2^28."""
+    N = N_LARGE
+    st = torch.cuda.current_stream()
+    f = torch.empty_like(x)
+    o = torch.empty_like(x)
+    y = torch.empty_like(x)
+    total = torch.zeros(4, dtype=torch.int32, device=x.device)
+    s, ws_bytes = ka.ka_workspace_size(N)
+    ws_t = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=x.device)
+    ws = (ws_t.data_ptr() + 255) // 256 * 256
+    ka.check(ka.ka_workspace_init(ws, ws_bytes, st.cuda_stream))
+    out = []
+    reps = 5
+    for i, t in enumerate(thresholds):
+        times = {"predicate": 0.0, "exclusive_scan": 0.0, "scatter": 0.0}
+        for r in range(reps + 2):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[0].record(st)
+            ka.check(ka.ka_predicate(x, N, None, ka.KA_PRED_LT, t, f, st.cuda_stream))
+            e[1].record(st)
+            ka.check(ka.ka_exclusive_scan(f, N, None, o, total, ws, ws_bytes, None, st.cuda_stream))
+            e[2].record(st)
+            ka.check(ka.ka_scatter(x, f, o, N, None, y, st.cuda_stream))
+            e[3].record(st)
+            torch.cuda.synchronize()
+            if r >= 2:
+                times["predicate"] += e[0].elapsed_time(e[1]) / reps
+                times["exclusive_scan"] += e[1].elapsed_time(e[2]) / reps
+                times["scatter"] += e[2].elapsed_time(e[3]) / reps
+        k = int(total[0].item()) & 0xFFFFFFFF
+        bytes_ = {"predicate": 8.0 * N, "exclusive_scan": 8.0 * N, "scatter": 12.0 * N + 4.0 * k}
+        ms = sum(times.values())
+        out.append({"s": SELECTIVITIES[i], "ms": round(ms, 4), "elements/s": N / (ms / 1000),
+                    "kernels": {kname: {"us": round(tv * 1000, 2),
+                                        "GB/s": round(bytes_[kname] / (tv / 1000) / 1e9, 1),
+                                        "frac": round(bytes_[kname] / (tv / 1000) / 1e9 / peak, 4)}
+                                for kname, tv in times.items()}})
+    return out
+
+
+def cpu_baseline_large(kept_gpu):
+    """The oracle's sequential loop on the host, one core, full-size input."""
+    import oracle
+    import ka_inputs as ki
+    N = N_LARGE
+    x = oracle.generate(SEED, N)
+    t0 = time.perf_counter()
+    ks = []
+    for s_ in SELECTIVITIES:
+        _, k = oracle.compact(x, "lt", ki.threshold_for(s_))
+        ks.append(k)
+    dt = time.perf_counter() - t0
+    return {"value": 3.0 * N / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
+            "host_cores_available": os.cpu_count(),
+            "sample": "full workload: N=2^28 at s=1%/50%/99%, one pass each (%.1f s)" % dt,
+            "counts_match_gpu": ks == list(kept_gpu)}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    """Reference arm: the CPU oracle on the same workload, bounded samples."""
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import ka_inputs as ki
+    K, W = args.steps, max(args.warmup, 3)
+    sample = 1 << 24 if K + W <= 100 else 1 << 22
+    x = oracle.generate(SEED, sample)
+    thresholds = [ki.threshold_for(s) for s in SELECTIVITIES]
+    for _ in range(W):
+        for t in thresholds:
+            oracle.compact(x, "lt", t)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        for t in thresholds:
+            oracle.compact(x, "lt", t)
+    dt = time.perf_counter() - t0
+    value = 3.0 * sample * K / dt
+    desc = "first 2^%d entries of the N=2^28 input per step, s=1%%/50%%/99%%" % (sample.bit_length() - 1)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world,
+        "steps": K, "warmup": W, "ms_per_step": dt * 1000.0 / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "large single compaction: N=2^28 uint32 uniform (SplitMix64 seed 2), keep x < t, "
+                               "t = floor(s 2^32), s = 1%, 50%, 99%", "n": N_LARGE,
+                   "selectivities": list(SELECTIVITIES), "parallelism": "single host core"},
+        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

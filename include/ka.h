@@ -1,0 +1,383 @@
+/*
+ * ka.h - C ABI of libka.so: order-preserving stream compaction run as composed
+ * kernel actors on GPU-resident data (GB300, sm_103a).
+ *
+ * The calls follow the programming model of Hiesgen, Charousset and Schmidt,
+ * "OpenCL Actors - Adding Data Parallelism to Actor-based Programming with CAF"
+ * (arXiv 1709.07781):
+ *   - a kernel actor wraps one data-parallel stage (Sec. 3.2, 3.4);
+ *   - messages carry references to device buffers, typed and sized, so the
+ *     next stage runs on the same memory (Sec. 3.5, the mem_ref type);
+ *   - actors compose as C = B (.) A, C(msg) = B(A(msg)) (Sec. 3.5);
+ *   - the first stage uploads, the last reads back and answers the requester
+ *     (Sec. 3.5);
+ *   - a configuration word carries the element count into a stage and the new
+ *     length out of a compaction (Sec. 4.1);
+ *   - a device reference cannot be serialised (Sec. 3.5, option (a)).
+ * The compaction itself is the one of Sec. 4.1: remove every entry that fails
+ * a test, keep the rest in order; the paper runs it as flag, prefix sum and
+ * move phases (Listing 5). Here it also exists as one fused single-pass kernel
+ * (the "several kernels inside one actor" alternative of Sec. 3.6).
+ *
+ * Conventions for every call:
+ *   - Every call returns a ka_status; outputs are written only on KA_OK.
+ *     No C++ exception crosses this boundary.
+ *   - "d_" arguments are device pointers (cudaMalloc, a pool, or a torch
+ *     tensor's data_ptr); "h_" arguments are host pointers. The library never
+ *     takes ownership of caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream). Kernel calls are asynchronous on that stream; device-side
+ *     failures (a look-back that timed out) are recorded in the workspace and
+ *     read back by ka_workspace_status.
+ *   - Element type is uint32. Lengths are uint64 in the API; a single array is
+ *     limited to 2^32 - 1 elements (device counts are uint32).
+ *   - Live lengths: where a call takes (n, d_n), d_n == NULL means n is the
+ *     live length; otherwise n is the capacity (it sizes the launch) and the
+ *     live length is min(*d_n, n), read on the device. This is how a stage
+ *     consumes the previous stage's result without a host round trip.
+ *   - Handles (ka_system, ka_ref, ka_actor, ka_request_h) are opaque and are
+ *     released by the caller with the matching release call.
+ */
+#ifndef KA_H
+#define KA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Status codes                                                             */
+/* ------------------------------------------------------------------------ */
+typedef int32_t ka_status;
+#define KA_OK                   0
+#define KA_E_ARG               -1  /* bad argument (null pointer, size, alias)          */
+#define KA_E_TYPE              -2  /* message does not match the actor's signature      */
+#define KA_E_OOM               -3  /* device or host allocation failed                  */
+#define KA_E_BUDGET            -4  /* request larger than the memory budget             */
+#define KA_E_STALE             -5  /* handle already released                           */
+#define KA_E_CUDA              -6  /* a CUDA runtime call failed                        */
+#define KA_E_DEVICE_TIMEOUT    -7  /* a bounded device-side wait gave up                */
+#define KA_E_CLOSED            -8  /* system or mailbox closed                          */
+#define KA_E_NOT_SERIALIZABLE  -9  /* device references never leave the process        */
+#define KA_E_TIMEOUT          -10  /* host-side wait (ka_receive) timed out             */
+#define KA_E_UNSUPPORTED      -11  /* option not supported                              */
+#define KA_E_INJECTED         -12  /* failure injected on the host by a test hook       */
+#define KA_E_WORKSPACE        -13  /* workspace too small or not initialised            */
+
+/* Text for a status code (static storage). */
+const char *ka_strerror(ka_status s);
+/* Library version: major * 100 + minor. */
+int32_t ka_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Predicates: which entries a compaction keeps (Sec. 4.1 removes entries    */
+/* equal to a given value; KA_PRED_NE is that case, the others generalise it */
+/* to a keep-test).                                                         */
+/* ------------------------------------------------------------------------ */
+typedef enum ka_pred_kind {
+    KA_PRED_AND_MASK_EQ0 = 0, /* keep (x & param) == 0                     */
+    KA_PRED_LT = 1,           /* keep x < param                            */
+    KA_PRED_TOPBITS_LT = 2,   /* keep (x >> 28) < param                    */
+    KA_PRED_POPC_ODD = 3,     /* keep popcount(x) odd (param ignored)      */
+    KA_PRED_MOD_NE0 = 4,      /* keep x % param != 0; param == 0: KA_E_ARG */
+    KA_PRED_NE = 5,           /* keep x != param                           */
+    KA_PRED_ALL = 6           /* keep every entry (a pure map stage)       */
+} ka_pred_kind;
+
+/* Value transform applied to each entry before its test; the transformed
+ * value is what is tested and written. */
+#define KA_XFORM_NONE 0u
+#define KA_XFORM_HASH 1u      /* x -> x * 2654435761 mod 2^32 */
+
+/* Tile shape of a tiled kernel: threads per block and items per thread.
+ * block in {128, 256, 512}, ipt in {4, 8, 16}, block * ipt <= 4096.
+ * A NULL tile, or {0, 0}, picks the library default (or the autotuned shape
+ * once ka_autotune has run for that kernel). */
+typedef struct ka_tile {
+    uint32_t block;
+    uint32_t ipt;
+} ka_tile;
+
+/* ------------------------------------------------------------------------ */
+/* Workspace of the single-pass kernels: a 256-byte header (tile ticket and  */
+/* launch epoch, device error word, spin limit) followed by one 64-bit       */
+/* status word per tile for the decoupled look-back. Caller-allocated device */
+/* memory; initialise once with ka_workspace_init, then reuse for any number */
+/* of launches ordered on one stream (each launch leaves it ready for the    */
+/* next). Launches that may overlap on the GPU need separate workspaces.     */
+/* ------------------------------------------------------------------------ */
+ka_status ka_workspace_size(uint64_t capacity, const ka_tile *tile, uint64_t *bytes);
+ka_status ka_workspace_init(void *d_ws, uint64_t bytes, void *stream);
+/* Synchronises `stream`, then reads the device error word: *device_status is
+ * KA_OK or the first device-side error (KA_E_DEVICE_TIMEOUT). */
+ka_status ka_workspace_status(const void *d_ws, void *stream, ka_status *device_status);
+/* Test hook: polls a look-back makes before it gives up (default 1 << 22,
+ * about a second with back-off). Asynchronous on `stream`. */
+ka_status ka_workspace_set_spin_limit(void *d_ws, uint32_t polls, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Stage kernels, called directly (no actor layer).                          */
+/* ------------------------------------------------------------------------ */
+
+/* Seeded input: d_out[i] = high 32 bits of SplitMix64(seed, i), where
+ * SplitMix64(seed, i) is the (i+1)-th output of the generator whose state
+ * starts at `seed` (Steele, Lea & Flood 2014). Stands in for the upload the
+ * paper's first stage performs (Sec. 3.5). */
+ka_status ka_generate(uint32_t *d_out, uint64_t n, uint64_t seed, void *stream);
+
+/* Hash map stage: d_out[i] = d_in[i] * 2654435761 mod 2^32 for i < live n.
+ * d_n_out (optional) receives the live n, so the output carries its length. */
+ka_status ka_map_hash(const uint32_t *d_in, uint64_t n, const uint32_t *d_n, uint32_t *d_out,
+                      uint32_t *d_n_out, void *stream);
+
+/* Phase 1 of Sec. 4.1 (flag map): d_flags[i] = P(x[i]) in {0, 1}, i < live n. */
+ka_status ka_predicate(const uint32_t *d_x, uint64_t n, const uint32_t *d_n, int32_t pred,
+                       uint32_t param, uint32_t *d_flags, void *stream);
+
+/* Phase 2 of Sec. 4.1 (prefix sum): d_out[i] = sum_{j<i} d_in[j] mod 2^32 for
+ * i < live n, and *d_total = the sum of all live entries (0 for n = 0).
+ * Single pass with decoupled look-back; needs a workspace. d_out may equal d_in. */
+ka_status ka_exclusive_scan(const uint32_t *d_in, uint64_t n, const uint32_t *d_n, uint32_t *d_out,
+                            uint32_t *d_total, void *d_ws, uint64_t ws_bytes, const ka_tile *tile,
+                            void *stream);
+
+/* Phase 3 of Sec. 4.1 (move): d_out[d_offsets[i]] = d_x[i] for every i < live n
+ * with d_flags[i] == 1. d_flags must hold 0/1 and d_offsets their exclusive
+ * prefix sum (what ka_predicate and ka_exclusive_scan produce). */
+ka_status ka_scatter(const uint32_t *d_x, const uint32_t *d_flags, const uint32_t *d_offsets,
+                     uint64_t n, const uint32_t *d_n, uint32_t *d_out, void *stream);
+
+/* Fused single-pass compaction (flag, scan and move in one kernel with
+ * decoupled look-back): d_out[0..k) = the entries of x (after `xform`) that
+ * pass the test, in input order; *d_count = k. Entries d_out[k..) are not
+ * written. d_out may equal d_in (in place). d_count must not alias d_n. */
+ka_status ka_compact(const uint32_t *d_in, uint64_t n, const uint32_t *d_n, int32_t pred,
+                     uint32_t param, uint32_t xform, uint32_t *d_out, uint32_t *d_count,
+                     void *d_ws, uint64_t ws_bytes, const ka_tile *tile, void *stream);
+
+/* Interleave of fuseFillsLiterals (Sec. 4.1, Listing 5): d_index[2i] =
+ * d_chunk_ids[i], d_index[2i+1] = d_literals[i] for i < live k; d_n_out
+ * (optional) receives 2 * live k. */
+ka_status ka_prepare_index(const uint32_t *d_chunk_ids, const uint32_t *d_literals, uint64_t k,
+                           const uint32_t *d_k, uint32_t *d_index, uint32_t *d_n_out, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched compaction: many independent instances in one persistent launch.  */
+/* ------------------------------------------------------------------------ */
+typedef struct ka_batch_item {
+    const uint32_t *in;     /* device input                                   */
+    uint32_t *out;          /* device output, room for n entries (may = in)   */
+    const uint32_t *n_ptr;  /* optional device live length (NULL: use n)      */
+    uint32_t *count;        /* device word receiving the kept count           */
+    uint32_t n;             /* length, or capacity when n_ptr is set          */
+    int32_t pred;           /* ka_pred_kind                                   */
+    uint32_t param;         /* predicate parameter                            */
+    uint32_t xform;         /* KA_XFORM_*                                     */
+} ka_batch_item;            /* 48 bytes */
+
+/* Workspace for up to `max_items` items whose tiles total at most
+ * ceil(total_capacity / tile) + max_items. */
+ka_status ka_batch_workspace_size(uint32_t max_items, uint64_t total_capacity, const ka_tile *tile,
+                                  uint64_t *bytes);
+/* d_items: device array of n_items descriptors (read on the device, so a
+ * captured CUDA graph can be replayed over new contents). `grid` = 0 picks one
+ * persistent block per SM slot. Two launches: a plan kernel (per-item tile
+ * offsets from the live lengths) and the persistent compaction kernel. */
+ka_status ka_compact_batch(const ka_batch_item *d_items, uint32_t n_items, uint64_t total_capacity,
+                           void *d_ws, uint64_t ws_bytes, const ka_tile *tile, uint32_t grid,
+                           void *stream);
+
+/* Seeded input for many buffers at once: out_i[j] = hi32(SplitMix64(seed_i, j)). */
+typedef struct ka_gen_item {
+    uint32_t *out;
+    uint64_t seed;
+    uint32_t n;
+    uint32_t pad;
+} ka_gen_item;              /* 24 bytes */
+ka_status ka_generate_batch(const ka_gen_item *d_items, uint32_t n_items, void *d_ws, uint64_t ws_bytes,
+                            void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Autotuner: times each tile shape of a kernel on the current device with   */
+/* CUDA events and keeps the fastest per size bucket (a power of two of n),  */
+/* in memory and in a small JSON cache file.                                 */
+/* ------------------------------------------------------------------------ */
+#define KA_KERNEL_COMPACT 0
+#define KA_KERNEL_SCAN    1
+#define KA_KERNEL_BATCH   2
+ka_status ka_autotune(int32_t kernel, uint64_t n, const char *cache_path, ka_tile *best,
+                      float *best_us, void *stream);
+/* Shape the library uses for (kernel, n) now (default or autotuned). */
+ka_status ka_tile_for(int32_t kernel, uint64_t n, ka_tile *tile);
+ka_status ka_autotune_load(const char *cache_path);
+
+/* ------------------------------------------------------------------------ */
+/* Actor layer (Sec. 3.2-3.5).                                              */
+/* ------------------------------------------------------------------------ */
+typedef struct ka_system ka_system;
+typedef struct ka_ref ka_ref;
+typedef struct ka_actor ka_actor;
+typedef struct ka_request_h ka_request_h;
+
+typedef struct ka_config {
+    int32_t device;              /* CUDA device ordinal                                */
+    int32_t debug;               /* 1: check the device error word after each request */
+    void *stream;                /* borrowed cudaStream_t; NULL: the system makes one */
+    uint64_t budget_bytes;       /* device memory budget of the pool (0: 64 GiB)      */
+    const char *autotune_cache;  /* JSON cache file to load, or NULL                  */
+} ka_config;
+
+typedef enum ka_dtype { KA_U32 = 0 } ka_dtype;
+typedef enum ka_access { KA_READ = 1, KA_WRITE = 2, KA_READ_WRITE = 3 } ka_access;
+
+ka_status ka_system_create(const ka_config *cfg, ka_system **out);
+/* Stops the dispatcher. Fails with KA_E_ARG while requests are in flight
+ * unless force != 0 (then they complete with KA_E_CLOSED). */
+ka_status ka_system_destroy(ka_system *sys, int32_t force);
+/* Bytes of pool memory held by live references. */
+ka_status ka_system_pool_bytes(ka_system *sys, uint64_t *in_use, uint64_t *budget);
+
+/* A reference to device memory (the paper's mem_ref<T>): element type, live
+ * length, capacity, access rights. ka_ref_wrap borrows caller memory (the
+ * caller keeps it alive until every request using it has been received);
+ * ka_ref_alloc takes memory from the system's pool and returns it when the
+ * last holder releases it. */
+ka_status ka_ref_wrap(ka_system *sys, void *d_ptr, uint64_t n, uint64_t capacity, ka_dtype dtype,
+                      ka_access access, ka_ref **out);
+ka_status ka_ref_alloc(ka_system *sys, uint64_t capacity, ka_dtype dtype, ka_ref **out);
+/* Live length (waits for the work that produces it). */
+ka_status ka_ref_count(ka_ref *ref, uint64_t *n);
+ka_status ka_ref_info(ka_ref *ref, void **d_ptr, uint64_t *capacity, int32_t *dtype, int32_t *access);
+ka_status ka_ref_retain(ka_ref *ref);
+ka_status ka_ref_release(ka_ref *ref);
+/* Device references are process-local: always KA_E_NOT_SERIALIZABLE. */
+ka_status ka_ref_serialize(const ka_ref *ref, void *buf, uint64_t cap, uint64_t *written);
+
+typedef enum ka_stage_kind {
+    KA_STAGE_GENERATE = 0,  /* () -> (x)          seed from the message          */
+    KA_STAGE_MAP_HASH = 1,  /* (x) -> (h)                                        */
+    KA_STAGE_PREDICATE = 2, /* (x) -> (x, f)                                     */
+    KA_STAGE_EXSCAN = 3,    /* (x, f) -> (x, f, o)   o's count word = total      */
+    KA_STAGE_SCATTER = 4,   /* (x, f, o) -> (y)                                  */
+    KA_STAGE_COMPACT = 5,   /* (x) -> (y)            fused single pass           */
+    KA_STAGE_PREPARE = 6,   /* (a, b) -> (index)     interleave, 2k entries      */
+    KA_STAGE_EMPTY = 7      /* (x) -> (x)            empty kernel, overhead probe */
+} ka_stage_kind;
+
+typedef struct ka_stage_desc {
+    int32_t kind;    /* ka_stage_kind                  */
+    int32_t pred;    /* ka_pred_kind (PREDICATE, COMPACT) */
+    uint32_t param;
+    uint32_t xform;  /* KA_XFORM_* (COMPACT)           */
+    ka_tile tile;    /* {0, 0}: default / autotuned    */
+} ka_stage_desc;
+
+ka_status ka_spawn_stage(ka_system *sys, const ka_stage_desc *desc, ka_actor **out);
+/* C = B (.) A: messages to C go to A, A's result goes to B (Sec. 3.5).
+ * KA_E_TYPE if A's result arity differs from B's input arity. The composite
+ * holds its own references to A and B. */
+ka_status ka_compose(ka_actor *b, ka_actor *a, ka_actor **c_out);
+/* Arity of an actor's input and result messages. */
+ka_status ka_actor_arity(ka_actor *actor, int32_t *in_refs, int32_t *out_refs);
+ka_status ka_actor_release(ka_actor *actor);
+
+#define KA_MSG_MAX_REFS 4
+typedef struct ka_msg {
+    uint32_t n_refs;
+    ka_ref *refs[KA_MSG_MAX_REFS];
+    /* value mode, in: the first stage uploads h_in[0..h_n) into a pool buffer
+     * that replaces refs[0] (Sec. 3.5: the first actor transfers the data). */
+    const uint32_t *h_in;
+    uint64_t h_n;
+    /* value mode, out: the last stage reads the result back into
+     * h_out[0..h_out_cap) (Sec. 3.5: the last actor reads back). */
+    uint32_t *h_out;
+    uint64_t h_out_cap;
+    uint64_t seed;       /* for KA_STAGE_GENERATE */
+    uint64_t gen_n;      /* for KA_STAGE_GENERATE */
+    /* filled by ka_receive */
+    uint64_t count;      /* live length of the result's first reference */
+    ka_status status;
+} ka_msg;
+
+/* Sends `in` to the actor and returns at once. The caller keeps ownership of
+ * the references in `in` (the request holds its own). */
+ka_status ka_request(ka_actor *actor, const ka_msg *in, ka_request_h **out);
+/* Waits up to timeout_ns (< 0: forever) for the response. On KA_OK, *out holds
+ * the result: its references (owned by the caller, release them) and count;
+ * in value mode the data is in h_out. A stage failure is returned as that
+ * stage's status; the request's references are released. The handle is freed
+ * by a KA_OK or error return, but not by KA_E_TIMEOUT (call again). */
+ka_status ka_receive(ka_request_h *req, int64_t timeout_ns, ka_msg *out);
+
+/* Host evaluation of the predicate exactly as the kernels evaluate it (after
+ * the library's canonicalisation, e.g. the division-free modulus test); lets
+ * a CPU test compare it with the plain definition. *keep = 0 or 1. */
+ka_status ka_debug_pred_keep(int32_t pred, uint32_t param, uint32_t x, int32_t *keep);
+
+/* Test hooks (host-side fault injection; no GPU fault involved). */
+ka_status ka_debug_fail_stage(ka_actor *stage_actor, int32_t fail_after);  /* -1: off */
+ka_status ka_debug_kill_dispatcher(ka_system *sys);
+typedef void (*ka_monitor_fn)(void *user, ka_status reason);
+/* Called once from the system's threads when the dispatcher dies (link/monitor
+ * notification, Sec. 2.1). */
+ka_status ka_system_monitor(ka_system *sys, ka_monitor_fn fn, void *user);
+
+/* Capture the composite's launch sequence for messages of the given input
+ * capacity into a CUDA graph, replayed for later requests of that shape. */
+ka_status ka_actor_enable_graph(ka_actor *actor, int32_t enable);
+
+/* ------------------------------------------------------------------------ */
+/* Request loop with continuous batching (serving).                          */
+/* ------------------------------------------------------------------------ */
+typedef struct ka_serve_stage {
+    int32_t pred;    /* ka_pred_kind; KA_PRED_ALL with KA_XFORM_HASH = hash map */
+    uint32_t param;
+    uint32_t xform;
+} ka_serve_stage;
+
+typedef struct ka_serve_request {
+    double arrival_s;            /* offset from the start of the run               */
+    uint64_t seed;               /* data: n entries of the seeded stream           */
+    uint32_t n;
+    uint32_t n_stages;           /* 1..4                                           */
+    ka_serve_stage stages[4];
+    uint32_t *h_out;             /* optional: final data copied here (value mode)  */
+    uint64_t h_out_cap;
+} ka_serve_request;
+
+typedef struct ka_serve_result {
+    double admit_s;              /* when the request was admitted                   */
+    double done_s;               /* when its result was ready on the host           */
+    uint32_t count;              /* final live length                               */
+    ka_status status;
+} ka_serve_result;
+
+typedef struct ka_serve_options {
+    uint32_t mode;               /* 0: continuous batching; 1: plain launches per request */
+    uint32_t max_inflight;       /* admitted requests at most (0: 4096)              */
+    uint64_t budget_bytes;       /* admission budget (0: the system's)               */
+    double time_scale;           /* arrival_s multiplier (1.0 = real time)           */
+    ka_tile tile;                /* batched kernel shape ({0,0}: autotuned/default)  */
+} ka_serve_options;
+
+typedef struct ka_serve_stats {
+    double wall_s;
+    uint64_t elements;           /* input elements of completed requests             */
+    uint64_t launches;           /* kernel launches issued (graph nodes counted)     */
+    uint64_t iterations;         /* batch iterations (mode 0)                        */
+    uint64_t peak_bytes;         /* peak admitted bytes                              */
+    uint32_t max_inflight_seen;
+    uint32_t rejected;           /* requests larger than the whole budget            */
+} ka_serve_stats;
+
+ka_status ka_serve_run(ka_system *sys, const ka_serve_request *reqs, uint32_t n_reqs,
+                       const ka_serve_options *opt, ka_serve_result *results, ka_serve_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KA_H */

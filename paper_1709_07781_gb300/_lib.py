@@ -1,0 +1,305 @@
+"""ctypes binding of libka.so: the C entry points of include/ka.h under the same
+names. Argument marshalling only: device pointers may be given as ints or as
+torch tensors (their data_ptr), streams as ints, torch streams, or None; every
+computation happens in the library's CUDA kernels.
+
+Calls return the C status code (0 = KA_OK); calls with C out-parameters return
+(status, value...). `check(status)` raises KaError for a non-zero status.
+The library must have been built (build.py, or __graft_entry__.build()); a
+missing library raises at import, and there is no other code path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libka.so")
+
+c_u32p = ctypes.POINTER(ctypes.c_uint32)
+c_vp = ctypes.c_void_p
+
+STATUS = {
+    0: "KA_OK", -1: "KA_E_ARG", -2: "KA_E_TYPE", -3: "KA_E_OOM", -4: "KA_E_BUDGET", -5: "KA_E_STALE",
+    -6: "KA_E_CUDA", -7: "KA_E_DEVICE_TIMEOUT", -8: "KA_E_CLOSED", -9: "KA_E_NOT_SERIALIZABLE",
+    -10: "KA_E_TIMEOUT", -11: "KA_E_UNSUPPORTED", -12: "KA_E_INJECTED", -13: "KA_E_WORKSPACE",
+}
+globals().update({v: k for k, v in STATUS.items()})
+
+PRED = {"and_mask_eq0": 0, "lt": 1, "topbits_lt": 2, "popc_odd": 3, "mod_ne0": 4, "ne": 5, "all": 6}
+KA_PRED_AND_MASK_EQ0, KA_PRED_LT, KA_PRED_TOPBITS_LT, KA_PRED_POPC_ODD, KA_PRED_MOD_NE0, KA_PRED_NE, KA_PRED_ALL = range(7)
+KA_XFORM_NONE, KA_XFORM_HASH = 0, 1
+KA_KERNEL_COMPACT, KA_KERNEL_SCAN, KA_KERNEL_BATCH = 0, 1, 2
+(KA_STAGE_GENERATE, KA_STAGE_MAP_HASH, KA_STAGE_PREDICATE, KA_STAGE_EXSCAN, KA_STAGE_SCATTER,
+ KA_STAGE_COMPACT, KA_STAGE_PREPARE, KA_STAGE_EMPTY) = range(8)
+KA_U32 = 0
+KA_READ, KA_WRITE, KA_READ_WRITE = 1, 2, 3
+KA_MSG_MAX_REFS = 4
+
+
+class KaError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__("%s (%d)%s" % (STATUS.get(status, "?"), status, (": " + what) if what else ""))
+
+
+def check(status, what: str = ""):
+    s = status[0] if isinstance(status, tuple) else status
+    if s != 0:
+        raise KaError(s, what)
+    return status
+
+
+class ka_tile(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_uint32), ("ipt", ctypes.c_uint32)]
+
+
+class ka_batch_item(ctypes.Structure):
+    _fields_ = [("in_", c_vp), ("out", c_vp), ("n_ptr", c_vp), ("count", c_vp), ("n", ctypes.c_uint32),
+                ("pred", ctypes.c_int32), ("param", ctypes.c_uint32), ("xform", ctypes.c_uint32)]
+
+
+class ka_gen_item(ctypes.Structure):
+    _fields_ = [("out", c_vp), ("seed", ctypes.c_uint64), ("n", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+
+
+class ka_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("debug", ctypes.c_int32), ("stream", c_vp),
+                ("budget_bytes", ctypes.c_uint64), ("autotune_cache", ctypes.c_char_p)]
+
+
+class ka_stage_desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("pred", ctypes.c_int32), ("param", ctypes.c_uint32),
+                ("xform", ctypes.c_uint32), ("tile", ka_tile)]
+
+
+class ka_msg(ctypes.Structure):
+    _fields_ = [("n_refs", ctypes.c_uint32), ("refs", c_vp * KA_MSG_MAX_REFS), ("h_in", c_u32p),
+                ("h_n", ctypes.c_uint64), ("h_out", c_u32p), ("h_out_cap", ctypes.c_uint64),
+                ("seed", ctypes.c_uint64), ("gen_n", ctypes.c_uint64), ("count", ctypes.c_uint64),
+                ("status", ctypes.c_int32)]
+
+
+class ka_serve_stage(ctypes.Structure):
+    _fields_ = [("pred", ctypes.c_int32), ("param", ctypes.c_uint32), ("xform", ctypes.c_uint32)]
+
+
+class ka_serve_request(ctypes.Structure):
+    _fields_ = [("arrival_s", ctypes.c_double), ("seed", ctypes.c_uint64), ("n", ctypes.c_uint32),
+                ("n_stages", ctypes.c_uint32), ("stages", ka_serve_stage * 4), ("h_out", c_u32p),
+                ("h_out_cap", ctypes.c_uint64)]
+
+
+class ka_serve_result(ctypes.Structure):
+    _fields_ = [("admit_s", ctypes.c_double), ("done_s", ctypes.c_double), ("count", ctypes.c_uint32),
+                ("status", ctypes.c_int32)]
+
+
+class ka_serve_options(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_uint32), ("max_inflight", ctypes.c_uint32), ("budget_bytes", ctypes.c_uint64),
+                ("time_scale", ctypes.c_double), ("tile", ka_tile)]
+
+
+class ka_serve_stats(ctypes.Structure):
+    _fields_ = [("wall_s", ctypes.c_double), ("elements", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("iterations", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
+                ("max_inflight_seen", ctypes.c_uint32), ("rejected", ctypes.c_uint32)]
+
+
+MONITOR_FN = ctypes.CFUNCTYPE(None, c_vp, ctypes.c_int32)
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "ka_strerror": (ctypes.c_char_p, [ctypes.c_int32]),
+    "ka_version": (ctypes.c_int32, []),
+    "ka_workspace_size": (ctypes.c_int32, [ctypes.c_uint64, ctypes.POINTER(ka_tile), ctypes.POINTER(ctypes.c_uint64)]),
+    "ka_workspace_init": (ctypes.c_int32, [c_vp, ctypes.c_uint64, c_vp]),
+    "ka_workspace_status": (ctypes.c_int32, [c_vp, c_vp, ctypes.POINTER(ctypes.c_int32)]),
+    "ka_workspace_set_spin_limit": (ctypes.c_int32, [c_vp, ctypes.c_uint32, c_vp]),
+    "ka_generate": (ctypes.c_int32, [c_vp, ctypes.c_uint64, ctypes.c_uint64, c_vp]),
+    "ka_map_hash": (ctypes.c_int32, [c_vp, ctypes.c_uint64, c_vp, c_vp, c_vp, c_vp]),
+    "ka_predicate": (ctypes.c_int32, [c_vp, ctypes.c_uint64, c_vp, ctypes.c_int32, ctypes.c_uint32, c_vp, c_vp]),
+    "ka_exclusive_scan": (ctypes.c_int32, [c_vp, ctypes.c_uint64, c_vp, c_vp, c_vp, c_vp, ctypes.c_uint64,
+                                           ctypes.POINTER(ka_tile), c_vp]),
+    "ka_scatter": (ctypes.c_int32, [c_vp, c_vp, c_vp, ctypes.c_uint64, c_vp, c_vp, c_vp]),
+    "ka_compact": (ctypes.c_int32, [c_vp, ctypes.c_uint64, c_vp, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32,
+                                    c_vp, c_vp, c_vp, ctypes.c_uint64, ctypes.POINTER(ka_tile), c_vp]),
+    "ka_prepare_index": (ctypes.c_int32, [c_vp, c_vp, ctypes.c_uint64, c_vp, c_vp, c_vp, c_vp]),
+    "ka_batch_workspace_size": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(ka_tile),
+                                                 ctypes.POINTER(ctypes.c_uint64)]),
+    "ka_compact_batch": (ctypes.c_int32, [c_vp, ctypes.c_uint32, ctypes.c_uint64, c_vp, ctypes.c_uint64,
+                                          ctypes.POINTER(ka_tile), ctypes.c_uint32, c_vp]),
+    "ka_generate_batch": (ctypes.c_int32, [c_vp, ctypes.c_uint32, c_vp, ctypes.c_uint64, c_vp]),
+    "ka_autotune": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_uint64, ctypes.c_char_p, ctypes.POINTER(ka_tile),
+                                     ctypes.POINTER(ctypes.c_float), c_vp]),
+    "ka_tile_for": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(ka_tile)]),
+    "ka_autotune_load": (ctypes.c_int32, [ctypes.c_char_p]),
+    "ka_system_create": (ctypes.c_int32, [ctypes.POINTER(ka_config), ctypes.POINTER(c_vp)]),
+    "ka_system_destroy": (ctypes.c_int32, [c_vp, ctypes.c_int32]),
+    "ka_system_pool_bytes": (ctypes.c_int32, [c_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+    "ka_ref_wrap": (ctypes.c_int32, [c_vp, c_vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.POINTER(c_vp)]),
+    "ka_ref_alloc": (ctypes.c_int32, [c_vp, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(c_vp)]),
+    "ka_ref_count": (ctypes.c_int32, [c_vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "ka_ref_info": (ctypes.c_int32, [c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(ctypes.c_uint64),
+                                     ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "ka_ref_retain": (ctypes.c_int32, [c_vp]),
+    "ka_ref_release": (ctypes.c_int32, [c_vp]),
+    "ka_ref_serialize": (ctypes.c_int32, [c_vp, c_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
+    "ka_spawn_stage": (ctypes.c_int32, [c_vp, ctypes.POINTER(ka_stage_desc), ctypes.POINTER(c_vp)]),
+    "ka_compose": (ctypes.c_int32, [c_vp, c_vp, ctypes.POINTER(c_vp)]),
+    "ka_actor_arity": (ctypes.c_int32, [c_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "ka_actor_release": (ctypes.c_int32, [c_vp]),
+    "ka_request": (ctypes.c_int32, [c_vp, ctypes.POINTER(ka_msg), ctypes.POINTER(c_vp)]),
+    "ka_receive": (ctypes.c_int32, [c_vp, ctypes.c_int64, ctypes.POINTER(ka_msg)]),
+    "ka_debug_pred_keep": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32,
+                                            ctypes.POINTER(ctypes.c_int32)]),
+    "ka_debug_fail_stage": (ctypes.c_int32, [c_vp, ctypes.c_int32]),
+    "ka_debug_kill_dispatcher": (ctypes.c_int32, [c_vp]),
+    "ka_system_monitor": (ctypes.c_int32, [c_vp, MONITOR_FN, c_vp]),
+    "ka_actor_enable_graph": (ctypes.c_int32, [c_vp, ctypes.c_int32]),
+    "ka_serve_run": (ctypes.c_int32, [c_vp, ctypes.POINTER(ka_serve_request), ctypes.c_uint32,
+                                      ctypes.POINTER(ka_serve_options), ctypes.POINTER(ka_serve_result),
+                                      ctypes.POINTER(ka_serve_stats)]),
+}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libka.so is not built (%s); run __graft_entry__.build() or "
+                      "python paper_1709_07781_gb300/build.py" % LIB_PATH)
+
+lib = ctypes.CDLL(LIB_PATH)
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+DECLARED = tuple(_SIGS)
+
+
+def ptr(x):
+    """Device/host pointer of an int, a torch tensor, a numpy array, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError("not a pointer: %r" % type(x))
+
+
+def stream_ptr(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _tile(t):
+    if t is None:
+        return None
+    if isinstance(t, ka_tile):
+        return ctypes.byref(t)
+    return ctypes.byref(ka_tile(int(t[0]), int(t[1])))
+
+
+def ka_strerror(status: int) -> str:
+    return lib.ka_strerror(status).decode()
+
+
+def ka_version() -> int:
+    return lib.ka_version()
+
+
+def ka_workspace_size(capacity: int, tile=None):
+    out = ctypes.c_uint64(0)
+    s = lib.ka_workspace_size(capacity, _tile(tile), ctypes.byref(out))
+    return s, out.value
+
+
+def ka_workspace_init(d_ws, nbytes: int, stream=None) -> int:
+    return lib.ka_workspace_init(ptr(d_ws), nbytes, stream_ptr(stream))
+
+
+def ka_workspace_status(d_ws, stream=None):
+    out = ctypes.c_int32(0)
+    s = lib.ka_workspace_status(ptr(d_ws), stream_ptr(stream), ctypes.byref(out))
+    return s, out.value
+
+
+def ka_workspace_set_spin_limit(d_ws, polls: int, stream=None) -> int:
+    return lib.ka_workspace_set_spin_limit(ptr(d_ws), polls, stream_ptr(stream))
+
+
+def ka_generate(d_out, n: int, seed: int, stream=None) -> int:
+    return lib.ka_generate(ptr(d_out), n, seed & (2**64 - 1), stream_ptr(stream))
+
+
+def ka_map_hash(d_in, n: int, d_n, d_out, d_n_out=None, stream=None) -> int:
+    return lib.ka_map_hash(ptr(d_in), n, ptr(d_n), ptr(d_out), ptr(d_n_out), stream_ptr(stream))
+
+
+def ka_predicate(d_x, n: int, d_n, pred: int, param: int, d_flags, stream=None) -> int:
+    return lib.ka_predicate(ptr(d_x), n, ptr(d_n), pred, param, ptr(d_flags), stream_ptr(stream))
+
+
+def ka_exclusive_scan(d_in, n: int, d_n, d_out, d_total, d_ws, ws_bytes: int, tile=None, stream=None) -> int:
+    return lib.ka_exclusive_scan(ptr(d_in), n, ptr(d_n), ptr(d_out), ptr(d_total), ptr(d_ws), ws_bytes,
+                                 _tile(tile), stream_ptr(stream))
+
+
+def ka_scatter(d_x, d_flags, d_offsets, n: int, d_n, d_out, stream=None) -> int:
+    return lib.ka_scatter(ptr(d_x), ptr(d_flags), ptr(d_offsets), n, ptr(d_n), ptr(d_out), stream_ptr(stream))
+
+
+def ka_compact(d_in, n: int, d_n, pred: int, param: int, xform: int, d_out, d_count, d_ws, ws_bytes: int,
+               tile=None, stream=None) -> int:
+    return lib.ka_compact(ptr(d_in), n, ptr(d_n), pred, param, xform, ptr(d_out), ptr(d_count), ptr(d_ws),
+                          ws_bytes, _tile(tile), stream_ptr(stream))
+
+
+def ka_prepare_index(d_chunk_ids, d_literals, k: int, d_k, d_index, d_n_out=None, stream=None) -> int:
+    return lib.ka_prepare_index(ptr(d_chunk_ids), ptr(d_literals), k, ptr(d_k), ptr(d_index), ptr(d_n_out),
+                                stream_ptr(stream))
+
+
+def ka_batch_workspace_size(max_items: int, total_capacity: int, tile=None):
+    out = ctypes.c_uint64(0)
+    s = lib.ka_batch_workspace_size(max_items, total_capacity, _tile(tile), ctypes.byref(out))
+    return s, out.value
+
+
+def ka_compact_batch(d_items, n_items: int, total_capacity: int, d_ws, ws_bytes: int, tile=None, grid: int = 0,
+                     stream=None) -> int:
+    return lib.ka_compact_batch(ptr(d_items), n_items, total_capacity, ptr(d_ws), ws_bytes, _tile(tile), grid,
+                                stream_ptr(stream))
+
+
+def ka_generate_batch(d_items, n_items: int, d_ws, ws_bytes: int, stream=None) -> int:
+    return lib.ka_generate_batch(ptr(d_items), n_items, ptr(d_ws), ws_bytes, stream_ptr(stream))
+
+
+def ka_autotune(kernel: int, n: int, cache_path=None, stream=None):
+    best = ka_tile(0, 0)
+    us = ctypes.c_float(0)
+    s = lib.ka_autotune(kernel, n, cache_path.encode() if cache_path else None, ctypes.byref(best),
+                        ctypes.byref(us), stream_ptr(stream))
+    return s, (best.block, best.ipt), us.value
+
+
+def ka_tile_for(kernel: int, n: int):
+    t = ka_tile(0, 0)
+    s = lib.ka_tile_for(kernel, n, ctypes.byref(t))
+    return s, (t.block, t.ipt)
+
+
+def ka_debug_pred_keep(pred: int, param: int, x: int):
+    out = ctypes.c_int32(0)
+    s = lib.ka_debug_pred_keep(pred, param, x, ctypes.byref(out))
+    return s, out.value
+
+
+def ka_autotune_load(cache_path: str) -> int:
+    return lib.ka_autotune_load(cache_path.encode())

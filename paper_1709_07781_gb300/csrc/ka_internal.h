@@ -1,0 +1,73 @@
+// Internal host-side declarations of libka (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/ka.h"
+#include "ka_dev.cuh"
+
+namespace ka {
+
+// Device properties of the current device, cached per ordinal.
+struct DeviceInfo {
+    int ordinal = -1;
+    int sm_count = 0;
+    int max_smem_optin = 0;
+};
+const DeviceInfo &device_info();
+
+// cudaError_t -> ka_status (records the CUDA error for ka_strerror detail).
+ka_status cuda_status(cudaError_t e);
+
+// Canonical device predicate for (kind, param). KA_E_ARG on an unknown kind
+// or a zero modulus.
+ka_status make_pred(int32_t kind, uint32_t param, PredDev *out);
+
+// Supported tile shapes.
+bool tile_supported(uint32_t block, uint32_t ipt);
+// Shape to use for `kernel` at size n: explicit shape, else autotuned, else default.
+ka_tile resolve_tile(int32_t kernel, uint64_t n, const ka_tile *requested);
+
+// Workspace layout for single-pass kernels.
+constexpr uint64_t kWsHeaderBytes = 256;
+inline uint64_t tiles_for(uint64_t n, uint32_t tile_elems) { return (n + tile_elems - 1) / tile_elems; }
+inline uint64_t workspace_bytes_for_tiles(uint64_t tiles) {
+    return kWsHeaderBytes + ((tiles * 8 + 255) / 256) * 256;
+}
+
+// Launchers shared by the C ABI and the actor runtime. All asynchronous.
+struct CompactLaunch {
+    const uint32_t *in;
+    uint32_t *out;
+    const uint32_t *n_ptr;
+    uint32_t *count;
+    uint64_t n;  // live length, or capacity when n_ptr is set
+    PredDev pred;
+    uint32_t mul;  // 1, or the hash multiplier
+    void *ws;
+    uint64_t ws_bytes;
+    ka_tile tile;
+};
+ka_status launch_compact(const CompactLaunch &L, cudaStream_t stream);
+
+ka_status launch_exclusive_scan(const uint32_t *in, uint64_t n, const uint32_t *n_ptr, uint32_t *out,
+                                uint32_t *total, void *ws, uint64_t ws_bytes, ka_tile tile,
+                                cudaStream_t stream);
+ka_status launch_scatter(const uint32_t *x, const uint32_t *flags, const uint32_t *offsets, uint64_t n,
+                         const uint32_t *n_ptr, uint32_t *out, cudaStream_t stream);
+ka_status launch_generate(uint32_t *out, uint64_t n, uint64_t seed, uint32_t *n_out, cudaStream_t stream);
+ka_status launch_map_hash(const uint32_t *in, uint64_t n, const uint32_t *n_ptr, uint32_t *out,
+                          uint32_t *n_out, cudaStream_t stream);
+ka_status launch_predicate(const uint32_t *x, uint64_t n, const uint32_t *n_ptr, const PredDev &pred,
+                           uint32_t *flags, uint32_t *n_out, cudaStream_t stream);
+ka_status launch_prepare_index(const uint32_t *a, const uint32_t *b, uint64_t k, const uint32_t *k_ptr,
+                               uint32_t *index, uint32_t *n_out, cudaStream_t stream);
+ka_status launch_copy_count(const uint32_t *n_ptr, uint64_t n, uint32_t *n_out, cudaStream_t stream);
+
+// Workspace validation (host side): size and alignment.
+ka_status check_workspace(const void *ws, uint64_t ws_bytes, uint64_t tiles_needed);
+
+constexpr uint32_t kHashMul = 2654435761u;
+
+}  // namespace ka

@@ -1,0 +1,113 @@
+"""The C ABI library without a GPU: it loads, exports every entry point that
+include/ka.h declares, and its host-only calls behave (no kernel runs here)."""
+import ctypes
+import os
+import re
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ka.h")
+
+
+@pytest.fixture(scope="module")
+def ka():
+    from paper_1709_07781_gb300 import build as kb
+    kb.build()
+    import paper_1709_07781_gb300 as m
+    return m
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(ka_[a-z0-9_]+)\s*\(", text)
+    return sorted({n for n in names if not n.endswith("_fn")})
+
+
+def test_every_declared_symbol_is_exported(ka):
+    names = declared_functions()
+    assert len(names) >= 40
+    lib = ctypes.CDLL(ka._lib.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    # and the binding covers every one of them under the same name
+    assert set(names) <= set(ka._lib.DECLARED), set(names) - set(ka._lib.DECLARED)
+
+
+def test_strerror_and_version(ka):
+    assert ka.ka_version() >= 100
+    assert "timed out" in ka.ka_strerror(ka.KA_E_DEVICE_TIMEOUT)
+    for code in ka._lib.STATUS:
+        assert ka.ka_strerror(code) != "unknown status"
+
+
+def test_workspace_size(ka):
+    s, b = ka.ka_workspace_size(1 << 28)
+    assert s == 0 and b >= 256 + 8 * ((1 << 28) // 512)
+    s, b2 = ka.ka_workspace_size(1 << 28, (256, 16))
+    assert s == 0 and 256 + 8 * ((1 << 28) // 4096) <= b2 < b
+    assert ka.ka_workspace_size(1 << 33)[0] == ka.KA_E_ARG
+    assert ka.ka_workspace_size(100, (100, 4))[0] == ka.KA_E_ARG
+
+
+def test_default_tiles(ka):
+    assert ka.ka_tile_for(ka.KA_KERNEL_COMPACT, 1 << 28) == (0, (256, 16))
+    s, t = ka.ka_tile_for(ka.KA_KERNEL_COMPACT, 1 << 20)
+    assert s == 0 and t[0] * t[1] <= 4096
+
+
+def test_autotune_cache_roundtrip(ka, tmp_path):
+    p = tmp_path / "tune.json"
+    p.write_text('{"entries": [\n  {"kernel": 0, "bucket": 17, "block": 128, "ipt": 8, "us": 3.5}\n]}\n')
+    assert ka.ka_autotune_load(str(p)) == 0
+    assert ka.ka_tile_for(ka.KA_KERNEL_COMPACT, 1 << 17) == (0, (128, 8))
+    assert ka.ka_autotune_load(str(tmp_path / "missing.json")) == ka.KA_E_ARG
+
+
+def test_kernel_predicates_match_the_oracle_definition(ka):
+    """The kernels' canonical predicates (x < p<<28 for the top-bits test, the
+    division-free multiple test) agree with the oracle's plain definitions."""
+    import oracle
+    import ka_inputs as ki
+    xs = list(map(int, ki.uniform_u32(5, 3000))) + [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 12, 0x7FFFFFFF, 0x80000000,
+                                                   0xFFFFFFFF, 0xFFFFFFFE, 0xFFFFFFFD, 0xFFFFFFFC, 3 * 1431655765]
+    cases = [("and_mask_eq0", 3), ("lt", 12345), ("popc_odd", 0), ("ne", 7), ("ne", 0)]
+    cases += [("topbits_lt", p) for p in (0, 1, 7, 8, 15, 16, 100)]
+    cases += [("mod_ne0", d) for d in (1, 2, 3, 4, 5, 6, 7, 12, 24, 96, 1000, 65536, 2**31, 2**31 + 1,
+                                       0xFFFFFFFF, 0xFFFFFFFE)]
+    for pred, param in cases:
+        for x in xs:
+            s, got = ka.ka_debug_pred_keep(ka.PRED[pred], param, x)
+            assert s == 0
+            assert got == oracle.keep(pred, param, x), (pred, param, x)
+    assert ka.ka_debug_pred_keep(ka.KA_PRED_MOD_NE0, 0, 5)[0] == ka.KA_E_ARG
+
+
+def test_references_cannot_be_serialised(ka):
+    buf = ctypes.create_string_buffer(16)
+    n = ctypes.c_uint64(0)
+    assert ka.lib.ka_ref_serialize(None, buf, 16, ctypes.byref(n)) == ka.KA_E_NOT_SERIALIZABLE
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """No fallback: importing the package without libka.so raises."""
+    import shutil
+    pkg = os.path.join(ROOT, "paper_1709_07781_gb300")
+    dst = tmp_path / "paper_1709_07781_gb300"
+    shutil.copytree(pkg, dst, ignore=shutil.ignore_patterns("_build", "__pycache__"))
+    r = subprocess.run([sys.executable, "-c", "import paper_1709_07781_gb300"], cwd=str(tmp_path),
+                       capture_output=True, text=True)
+    assert r.returncode != 0 and "libka.so is not built" in r.stderr
+
+
+def test_product_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1709_07781_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cpp", ".h", ".cuh")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "ka_oracle" not in text, f
