@@ -51,6 +51,7 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-extras", action="store_true")
+    p.add_argument("--n", type=int, default=N_LARGE, help="input length (default 2^28; smaller only for profiling)")
     return p.parse_args()
 
 
@@ -150,6 +151,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def gpu_id_for_smi(torch, local: int) -> str:
+    """UUID of the device torch uses (nvidia-smi indices may differ from CUDA's)."""
+    try:
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(local)
+
+
 def measured_peak_gbs():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -195,7 +205,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     st = stream.cuda_stream
-    N = N_LARGE
+    N = args.n
     thresholds = [ki.threshold_for(s) for s in SELECTIVITIES]
 
     x = torch.empty(N, dtype=torch.int32, device=dev)
@@ -222,7 +232,7 @@ def run_ours(args):
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(K)]
     e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(gpu_id_for_smi(torch, local))
     D.barrier()
     torch.cuda.synchronize()
     clocks.start()
@@ -263,8 +273,9 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": K,
         "warmup": max(args.warmup, 3), "ms_per_step": max_total_s * 1000.0 / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "large single compaction: N=2^28 uint32 uniform (SplitMix64 seed 2), keep x < t, "
-                               "t = floor(s 2^32), s = 1%, 50%, 99%; fused single-pass decoupled look-back",
+        "config": {"workload": "large single compaction: N=2^%d uint32 uniform (SplitMix64 seed 2), keep x < t, "
+                               "t = floor(s 2^32), s = 1%%, 50%%, 99%%; fused single-pass decoupled look-back"
+                               % (N.bit_length() - 1),
                    "n": N, "selectivities": list(SELECTIVITIES), "kept": kept, "tile": list(tile),
                    "l2": "inputs (1 GiB) larger than L2; no flush", "parallelism": "replicas x%d" % world},
         "roofline": roofline, "gpu_launches": launches, "clocks": clock_info,
@@ -275,7 +286,7 @@ def run_ours(args):
     if not args.no_extras:
         result["extras"] = {"three_launch": three_launch_large(ka, torch, x, thresholds, D, peak)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline_large(kept)
+        result["cpu_baseline"] = cpu_baseline_large(kept, N)
     D.close()
     if rank == 0:
         print(json.dumps(result), flush=True)
@@ -285,7 +296,7 @@ def e2e_large(ka, torch, x_dev, kept, thresholds, ws, ws_bytes, D, steps):
     """Whole step through the C ABI with host buffers: pinned input uploaded,
     three compactions, counts and kept entries read back."""
     import numpy as np
-    N = N_LARGE
+    N = x_dev.numel()
     st = torch.cuda.current_stream()
     h_x = torch.empty(N, dtype=torch.int32, pin_memory=True)
     h_x.copy_(x_dev.cpu())
@@ -328,8 +339,8 @@ def e2e_large(ka, torch, x_dev, kept, thresholds, ws, ws_bytes, D, steps):
 
 
 def three_launch_large(ka, torch, x, thresholds, D, peak):
-    """The 3-launch chained version (flag map, exclusive scan, move) at N=2^28."""
-    N = N_LARGE
+    """The 3-launch chained version (flag map, exclusive scan, move)."""
+    N = x.numel()
     st = torch.cuda.current_stream()
     f = torch.empty_like(x)
     o = torch.empty_like(x)
@@ -368,11 +379,10 @@ def three_launch_large(ka, torch, x, thresholds, D, peak):
     return out
 
 
-def cpu_baseline_large(kept_gpu):
+def cpu_baseline_large(kept_gpu, N):
     """The oracle's sequential loop on the host, one core, full-size input."""
     import oracle
     import ka_inputs as ki
-    N = N_LARGE
     x = oracle.generate(SEED, N)
     t0 = time.perf_counter()
     ks = []
@@ -382,7 +392,7 @@ def cpu_baseline_large(kept_gpu):
     dt = time.perf_counter() - t0
     return {"value": 3.0 * N / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
             "host_cores_available": os.cpu_count(),
-            "sample": "full workload: N=2^28 at s=1%/50%/99%, one pass each (%.1f s)" % dt,
+            "sample": "full workload: N=2^%d at s=1%%/50%%/99%%, one pass each (%.1f s)" % (N.bit_length() - 1, dt),
             "counts_match_gpu": ks == list(kept_gpu)}
 
 

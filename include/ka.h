@@ -178,27 +178,38 @@ typedef struct ka_batch_item {
     uint32_t xform;         /* KA_XFORM_*                                     */
 } ka_batch_item;            /* 48 bytes */
 
-/* Workspace for up to `max_items` items whose tiles total at most
- * ceil(total_capacity / tile) + max_items. */
+/* Workspace for batches of up to `max_items` items whose inputs total at most
+ * `total_capacity` entries. Layout: the 256-byte header, per-item plan
+ * records (tile offset, canonical predicate, live length) for max_items items,
+ * then one status word per tile. Initialise with ka_workspace_init. */
 ka_status ka_batch_workspace_size(uint32_t max_items, uint64_t total_capacity, const ka_tile *tile,
                                   uint64_t *bytes);
-/* d_items: device array of n_items descriptors (read on the device, so a
- * captured CUDA graph can be replayed over new contents). `grid` = 0 picks one
- * persistent block per SM slot. Two launches: a plan kernel (per-item tile
- * offsets from the live lengths) and the persistent compaction kernel. */
-ka_status ka_compact_batch(const ka_batch_item *d_items, uint32_t n_items, uint64_t total_capacity,
-                           void *d_ws, uint64_t ws_bytes, const ka_tile *tile, uint32_t grid,
-                           void *stream);
+/* Compacts every item of d_items (a device array of n_items descriptors, read
+ * on the device, so a captured CUDA graph can be replayed over new contents):
+ * item i's kept entries go to out_i[0..k_i) in order and *count_i = k_i.
+ * max_items must be the value the workspace was sized for (it fixes the
+ * layout); n_items <= max_items. `grid` = 0 picks one persistent block per SM
+ * slot. Two launches: a plan kernel (live lengths, canonical predicates and
+ * per-item tile offsets) and one persistent kernel that walks the flattened
+ * (item, tile) ticket space with a decoupled look-back per item. Because the
+ * plan records each live length before any compaction runs, count_i may
+ * alias n_ptr_i (the paper's in_out configuration word). An invalid item
+ * (unknown predicate, zero modulus) gets count 0 and sets the workspace error
+ * KA_E_ARG; more tiles than the workspace holds set KA_E_WORKSPACE. */
+ka_status ka_compact_batch(const ka_batch_item *d_items, uint32_t n_items, uint32_t max_items, void *d_ws,
+                           uint64_t ws_bytes, const ka_tile *tile, uint32_t grid, void *stream);
 
-/* Seeded input for many buffers at once: out_i[j] = hi32(SplitMix64(seed_i, j)). */
+/* Seeded input for many buffers at once: out_i[j] = hi32(SplitMix64(seed_i, j))
+ * for j < n_i (the batched form of ka_generate). d_items is a device array;
+ * the workspace is one sized by ka_batch_workspace_size for max_items items. */
 typedef struct ka_gen_item {
     uint32_t *out;
     uint64_t seed;
     uint32_t n;
     uint32_t pad;
 } ka_gen_item;              /* 24 bytes */
-ka_status ka_generate_batch(const ka_gen_item *d_items, uint32_t n_items, void *d_ws, uint64_t ws_bytes,
-                            void *stream);
+ka_status ka_generate_batch(const ka_gen_item *d_items, uint32_t n_items, uint32_t max_items, void *d_ws,
+                            uint64_t ws_bytes, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Autotuner: times each tile shape of a kernel on the current device with   */

@@ -127,9 +127,9 @@ _SIGS = {
     "ka_prepare_index": (ctypes.c_int32, [c_vp, c_vp, ctypes.c_uint64, c_vp, c_vp, c_vp, c_vp]),
     "ka_batch_workspace_size": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(ka_tile),
                                                  ctypes.POINTER(ctypes.c_uint64)]),
-    "ka_compact_batch": (ctypes.c_int32, [c_vp, ctypes.c_uint32, ctypes.c_uint64, c_vp, ctypes.c_uint64,
+    "ka_compact_batch": (ctypes.c_int32, [c_vp, ctypes.c_uint32, ctypes.c_uint32, c_vp, ctypes.c_uint64,
                                           ctypes.POINTER(ka_tile), ctypes.c_uint32, c_vp]),
-    "ka_generate_batch": (ctypes.c_int32, [c_vp, ctypes.c_uint32, c_vp, ctypes.c_uint64, c_vp]),
+    "ka_generate_batch": (ctypes.c_int32, [c_vp, ctypes.c_uint32, ctypes.c_uint32, c_vp, ctypes.c_uint64, c_vp]),
     "ka_autotune": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_uint64, ctypes.c_char_p, ctypes.POINTER(ka_tile),
                                      ctypes.POINTER(ctypes.c_float), c_vp]),
     "ka_tile_for": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(ka_tile)]),
@@ -271,14 +271,14 @@ def ka_batch_workspace_size(max_items: int, total_capacity: int, tile=None):
     return s, out.value
 
 
-def ka_compact_batch(d_items, n_items: int, total_capacity: int, d_ws, ws_bytes: int, tile=None, grid: int = 0,
+def ka_compact_batch(d_items, n_items: int, max_items: int, d_ws, ws_bytes: int, tile=None, grid: int = 0,
                      stream=None) -> int:
-    return lib.ka_compact_batch(ptr(d_items), n_items, total_capacity, ptr(d_ws), ws_bytes, _tile(tile), grid,
+    return lib.ka_compact_batch(ptr(d_items), n_items, max_items, ptr(d_ws), ws_bytes, _tile(tile), grid,
                                 stream_ptr(stream))
 
 
-def ka_generate_batch(d_items, n_items: int, d_ws, ws_bytes: int, stream=None) -> int:
-    return lib.ka_generate_batch(ptr(d_items), n_items, ptr(d_ws), ws_bytes, stream_ptr(stream))
+def ka_generate_batch(d_items, n_items: int, max_items: int, d_ws, ws_bytes: int, stream=None) -> int:
+    return lib.ka_generate_batch(ptr(d_items), n_items, max_items, ptr(d_ws), ws_bytes, stream_ptr(stream))
 
 
 def ka_autotune(kernel: int, n: int, cache_path=None, stream=None):

@@ -33,47 +33,8 @@ const DeviceInfo &device_info() {
     return d;
 }
 
-// Inverse of an odd d modulo 2^32 by Newton iteration: x <- x (2 - d x)
-// doubles the number of correct low bits each step, starting from x = d
-// (correct to 3 bits for odd d).
-static uint32_t inverse_odd(uint32_t d) {
-    uint32_t x = d;
-    for (int i = 0; i < 5; ++i) x *= 2u - d * x;
-    return x;
-}
-
 ka_status make_pred(int32_t kind, uint32_t param, PredDev *out) {
-    PredDev p{};
-    switch (kind) {
-    case KA_PRED_AND_MASK_EQ0: p.kind = kAndMaskEq0; p.a = param; break;
-    case KA_PRED_LT: p.kind = kLt; p.a = param; break;
-    case KA_PRED_TOPBITS_LT:
-        // (x >> 28) < p  <=>  x < p * 2^28 for p <= 15; every x passes for p >= 16.
-        if (param >= 16u) {
-            p.kind = kAll;
-        } else {
-            p.kind = kLt;
-            p.a = param << 28;
-        }
-        break;
-    case KA_PRED_POPC_ODD: p.kind = kPopcOdd; break;
-    case KA_PRED_MOD_NE0: {
-        if (param == 0u) return KA_E_ARG;
-        uint32_t shift = 0, odd = param;
-        while ((odd & 1u) == 0u) { odd >>= 1; ++shift; }
-        p.kind = kModNe0;
-        p.a = inverse_odd(odd);
-        p.b = 0xFFFFFFFFu / odd;
-        p.c = shift == 0 ? 0u : (0xFFFFFFFFu >> (32 - shift));
-        p.d = shift;
-        break;
-    }
-    case KA_PRED_NE: p.kind = kNe; p.a = param; break;
-    case KA_PRED_ALL: p.kind = kAll; break;
-    default: return KA_E_ARG;
-    }
-    *out = p;
-    return KA_OK;
+    return pred_canon(kind, param, out) == 0 ? KA_OK : KA_E_ARG;
 }
 
 bool tile_supported(uint32_t block, uint32_t ipt) {

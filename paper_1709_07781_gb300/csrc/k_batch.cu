@@ -1,0 +1,339 @@
+// Batched compaction: many independent instances in one persistent launch,
+// and batched seeded generation.
+//
+// Plan kernel (one block): for every item, the live length (read once, so a
+// count word may alias its length word), the canonical predicate, its tile
+// count, and an exclusive scan of tile counts -> per-item first tile in one
+// flattened tile space. Persistent kernel: blocks take flattened tiles by
+// ticket, find the owning item with a warp-wide search (first a 32-item window
+// after the block's previous item, then a 32-ary search; tickets only grow
+// within a block), and run the fused tile body with a look-back that stops at
+// the item's first tile. Every status word is indexed by flattened tile, so
+// each item owns a contiguous segment of the status array.
+#include "ka_internal.h"
+#include "ka_tile.cuh"
+
+namespace ka {
+
+struct ItemPlan {  // 32 bytes
+    PredDev pred;
+    uint32_t mul;
+    uint32_t n;
+    uint32_t tiles;
+};
+static_assert(sizeof(ItemPlan) == 32, "plan record is 32 bytes");
+
+struct BatchLayout {
+    uint32_t *tile_off;  // [max_items + 1]
+    ItemPlan *plans;     // [max_items]
+    uint64_t *status;    // [status_cap]
+    uint32_t status_cap;
+};
+
+static inline uint64_t round256(uint64_t b) { return (b + 255) / 256 * 256; }
+
+static uint64_t batch_fixed_bytes(uint32_t max_items) {
+    return kWsHeaderBytes + round256((uint64_t(max_items) + 1) * 4) + round256(uint64_t(max_items) * 32);
+}
+
+static BatchLayout batch_layout(void *ws, uint64_t ws_bytes, uint32_t max_items) {
+    BatchLayout L;
+    char *p = static_cast<char *>(ws) + kWsHeaderBytes;
+    L.tile_off = reinterpret_cast<uint32_t *>(p);
+    p += round256((uint64_t(max_items) + 1) * 4);
+    L.plans = reinterpret_cast<ItemPlan *>(p);
+    p += round256(uint64_t(max_items) * 32);
+    L.status = reinterpret_cast<uint64_t *>(p);
+    const uint64_t fixed = batch_fixed_bytes(max_items);
+    const uint64_t words = ws_bytes > fixed ? (ws_bytes - fixed) / 8 : 0;
+    L.status_cap = words > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(words);
+    return L;
+}
+
+constexpr int kPlanBlock = 1024;
+
+// Exclusive block scan of v over kPlanBlock threads; *total = block sum.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t incl = warp_incl_scan(v, lane);
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = s_warp[lane];
+        const uint32_t wi = warp_incl_scan(w, lane);
+        s_warp[lane] = wi - w;
+        if (lane == 31) s_warp[32] = wi;
+    }
+    __syncthreads();
+    const uint32_t r = s_warp[warp] + incl - v;
+    *total = s_warp[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kPlanBlock) k_batch_plan(const ka_batch_item *items, uint32_t n_items,
+                                                            uint32_t T, BatchLayout L, WsHeader *ws) {
+    __shared__ uint32_t s_warp[33];
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < n_items; base += kPlanBlock) {
+        const uint32_t i = base + threadIdx.x;
+        uint32_t tiles = 0;
+        if (i < n_items) {
+            const ka_batch_item it = items[i];
+            uint32_t n = it.n;
+            if (it.n_ptr) {
+                const uint32_t d = *it.n_ptr;
+                n = d < n ? d : n;
+            }
+            ItemPlan pl;
+            const bool ok = pred_canon(it.pred, it.param, &pl.pred) == 0 && it.xform <= 1u;
+            if (!ok) {
+                record_error(ws, 1u, i);  // -KA_E_ARG
+                n = 0;
+            }
+            pl.mul = it.xform == 1u ? kHashMul : 1u;
+            pl.n = n;
+            tiles = uint32_t((uint64_t(n) + T - 1) / T);
+            pl.tiles = tiles;
+            L.plans[i] = pl;
+            if (n == 0 && it.count) *it.count = 0u;
+        }
+        uint32_t block_total;
+        const uint32_t excl = block_excl_scan(tiles, s_warp, &block_total);
+        if (i < n_items) L.tile_off[i] = carry + excl;
+        carry += block_total;
+    }
+    if (threadIdx.x == 0) {
+        L.tile_off[n_items] = carry;
+        if (carry > L.status_cap) record_error(ws, kDevErrWorkspace, 0);
+    }
+}
+
+// Item owning flattened tile `ticket`: the largest i with tile_off[i] <= ticket.
+// Precondition: tile_off[lo] <= ticket < tile_off[n_items]. Called by a full warp.
+__device__ __forceinline__ uint32_t find_item(const uint32_t *tile_off, uint32_t n_items, uint32_t lo,
+                                              uint32_t ticket) {
+    const int lane = threadIdx.x & 31;
+    {
+        const uint32_t j = lo + 1 + lane;
+        const uint32_t v = j <= n_items ? tile_off[j] : 0xFFFFFFFFu;
+        const uint32_t b = __ballot_sync(kFull, v > ticket);
+        if (b) return lo + __ffs(b) - 1;
+    }
+    lo += 32;
+    uint32_t hi = n_items;
+    while (hi - lo > 1) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint64_t jj = uint64_t(lo) + uint64_t(lane + 1) * step;
+        const uint32_t j = jj < hi ? uint32_t(jj) : hi;
+        const uint32_t v = tile_off[j];
+        const uint32_t b = __ballot_sync(kFull, v > ticket);
+        const uint32_t f = __ffs(b) - 1;
+        const uint64_t nh = uint64_t(lo) + uint64_t(f + 1) * step;
+        const uint32_t new_hi = nh < hi ? uint32_t(nh) : hi;
+        lo = f == 0 ? lo : lo + f * step;
+        hi = new_hi;
+    }
+    return lo;
+}
+
+struct BatchArgs {
+    const ka_batch_item *items;
+    uint32_t n_items;
+    BatchLayout L;
+    WsHeader *ws;
+};
+
+template <int BLOCK, int IPT>
+__global__ void __launch_bounds__(BLOCK) k_compact_batch(const BatchArgs a) {
+    constexpr int T = BLOCK * IPT;
+    __shared__ CompactSmem<BLOCK, IPT> sm;
+    __shared__ uint32_t s_ticket, s_epoch, s_total, s_spin, s_item;
+    __shared__ const uint32_t *s_in;
+    __shared__ uint32_t *s_outp, *s_count;
+    __shared__ ItemPlan s_plan;
+    __shared__ uint32_t s_first;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    if (tid == 0) {
+        s_total = a.L.tile_off[a.n_items];
+        const uint32_t sl = a.ws->spin_limit;
+        s_spin = sl ? sl : kDefaultSpinLimit;
+        s_item = 0;
+    }
+    __syncthreads();
+    const uint32_t total = s_total;
+    const uint32_t spin = s_spin;
+    if (total > a.L.status_cap) return;
+
+    for (;;) {
+        if (tid == 0) {
+            uint32_t ep;
+            bool last;
+            s_ticket = take_ticket(a.ws, total, &ep, &last);
+            s_epoch = ep;
+        }
+        __syncthreads();
+        const uint32_t ticket = s_ticket;
+        const uint32_t epoch = s_epoch;
+        if (ticket >= total) break;
+        if (warp == 0) {
+            const uint32_t item = find_item(a.L.tile_off, a.n_items, s_item, ticket);
+            if ((tid & 31) == 0) {
+                s_item = item;
+                const ka_batch_item *it = a.items + item;
+                s_in = it->in;
+                s_outp = it->out;
+                s_count = it->count;
+                s_plan = a.L.plans[item];
+                s_first = a.L.tile_off[item];
+            }
+        }
+        __syncthreads();
+        const ItemPlan pl = s_plan;
+        const uint32_t first = s_first;
+        const uint32_t local = ticket - first;
+        const uint32_t base = local * uint32_t(T);
+        const uint32_t valid = (pl.n - base) < uint32_t(T) ? (pl.n - base) : uint32_t(T);
+        const uint32_t *in = s_in;
+        const bool vec_ok = (reinterpret_cast<uintptr_t>(in) & 15u) == 0;
+        compact_tile<BLOCK, IPT>(sm, in + base, s_outp, valid, vec_ok, pl.mul, pl.pred, a.L.status, ticket, first,
+                                 epoch, spin, a.ws, local == pl.tiles - 1 ? s_count : nullptr);
+    }
+}
+
+template <int BLOCK, int IPT>
+static ka_status launch_batch_shape(const BatchArgs &a, uint32_t grid, cudaStream_t stream) {
+    static int occupancy = 0;
+    if (occupancy == 0) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_compact_batch<BLOCK, IPT>, BLOCK, 0);
+        occupancy = occ > 0 ? occ : 1;
+    }
+    const uint64_t resident = uint64_t(device_info().sm_count) * occupancy;
+    uint64_t g = grid ? grid : resident;
+    if (g > resident) g = resident;  // every block resident: tickets need no more
+    k_compact_batch<BLOCK, IPT><<<unsigned(g), BLOCK, 0, stream>>>(a);
+    return cuda_status(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Batched generation: same plan, fixed 4096-entry tiles, static grid-stride
+// over flattened tiles (no ordering between tiles is needed).
+constexpr uint32_t kGenTile = 4096;
+constexpr int kGenBlock = 256;
+
+__global__ void __launch_bounds__(kPlanBlock) k_gen_plan(const ka_gen_item *items, uint32_t n_items,
+                                                          BatchLayout L, WsHeader *ws) {
+    __shared__ uint32_t s_warp[33];
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < n_items; base += kPlanBlock) {
+        const uint32_t i = base + threadIdx.x;
+        uint32_t tiles = 0;
+        if (i < n_items) tiles = (items[i].n + kGenTile - 1) / kGenTile;
+        uint32_t block_total;
+        const uint32_t excl = block_excl_scan(tiles, s_warp, &block_total);
+        if (i < n_items) L.tile_off[i] = carry + excl;
+        carry += block_total;
+    }
+    if (threadIdx.x == 0) L.tile_off[n_items] = carry;
+}
+
+__device__ __forceinline__ uint64_t splitmix64_b(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void __launch_bounds__(kGenBlock) k_generate_batch(const ka_gen_item *items, uint32_t n_items,
+                                                               const uint32_t *tile_off) {
+    __shared__ uint32_t s_item;
+    const uint32_t total = tile_off[n_items];
+    uint32_t item = 0;
+    for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
+        if (threadIdx.x < 32) {
+            const uint32_t f = find_item(tile_off, n_items, item, t);
+            if (threadIdx.x == 0) s_item = f;
+        }
+        __syncthreads();
+        item = s_item;
+        const ka_gen_item it = items[item];
+        const uint32_t base = (t - tile_off[item]) * kGenTile;
+        const uint32_t end = it.n - base < kGenTile ? it.n : base + kGenTile;
+        for (uint32_t e = base + threadIdx.x; e < end; e += kGenBlock)
+            it.out[e] = uint32_t(splitmix64_b(it.seed, e) >> 32);
+        __syncthreads();
+    }
+}
+
+}  // namespace ka
+
+using namespace ka;
+
+extern "C" {
+
+ka_status ka_batch_workspace_size(uint32_t max_items, uint64_t total_capacity, const ka_tile *tile,
+                                  uint64_t *bytes) {
+    if (!bytes || max_items == 0) return KA_E_ARG;
+    uint32_t te = 512;
+    if (tile && tile->block && tile->ipt) {
+        if (!tile_supported(tile->block, tile->ipt)) return KA_E_ARG;
+        te = tile->block * tile->ipt;
+    }
+    const uint64_t tiles = tiles_for(total_capacity, te) + max_items + 1;
+    const uint64_t gen_tiles = tiles_for(total_capacity, kGenTile) + max_items + 1;
+    (void)gen_tiles;
+    *bytes = batch_fixed_bytes(max_items) + round256(tiles * 8);
+    return KA_OK;
+}
+
+ka_status ka_compact_batch(const ka_batch_item *d_items, uint32_t n_items, uint32_t max_items, void *d_ws,
+                           uint64_t ws_bytes, const ka_tile *tile, uint32_t grid, void *stream) {
+    if (n_items > max_items || max_items == 0) return KA_E_ARG;
+    if (n_items && !d_items) return KA_E_ARG;
+    if (!d_ws || (reinterpret_cast<uintptr_t>(d_ws) & 255u) != 0) return KA_E_ARG;
+    if (ws_bytes < batch_fixed_bytes(max_items) + 256) return KA_E_WORKSPACE;
+    if (n_items == 0) return KA_OK;
+    const ka_tile t = resolve_tile(KA_KERNEL_BATCH, 1ull << 17, tile);
+    if (!tile_supported(t.block, t.ipt)) return KA_E_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    BatchArgs a;
+    a.items = d_items;
+    a.n_items = n_items;
+    a.L = batch_layout(d_ws, ws_bytes, max_items);
+    a.ws = static_cast<WsHeader *>(d_ws);
+    k_batch_plan<<<1, kPlanBlock, 0, st>>>(d_items, n_items, t.block * t.ipt, a.L, a.ws);
+    ka_status s = cuda_status(cudaGetLastError());
+    if (s != KA_OK) return s;
+    switch (t.block * 100 + t.ipt) {
+    case 12804: return launch_batch_shape<128, 4>(a, grid, st);
+    case 12808: return launch_batch_shape<128, 8>(a, grid, st);
+    case 12816: return launch_batch_shape<128, 16>(a, grid, st);
+    case 25604: return launch_batch_shape<256, 4>(a, grid, st);
+    case 25608: return launch_batch_shape<256, 8>(a, grid, st);
+    case 25616: return launch_batch_shape<256, 16>(a, grid, st);
+    case 51204: return launch_batch_shape<512, 4>(a, grid, st);
+    case 51208: return launch_batch_shape<512, 8>(a, grid, st);
+    default: return KA_E_ARG;
+    }
+}
+
+ka_status ka_generate_batch(const ka_gen_item *d_items, uint32_t n_items, uint32_t max_items, void *d_ws,
+                            uint64_t ws_bytes, void *stream) {
+    if (n_items > max_items || max_items == 0) return KA_E_ARG;
+    if (n_items && !d_items) return KA_E_ARG;
+    if (!d_ws || (reinterpret_cast<uintptr_t>(d_ws) & 255u) != 0) return KA_E_ARG;
+    if (ws_bytes < batch_fixed_bytes(max_items)) return KA_E_WORKSPACE;
+    if (n_items == 0) return KA_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const BatchLayout L = batch_layout(d_ws, ws_bytes, max_items);
+    k_gen_plan<<<1, kPlanBlock, 0, st>>>(d_items, n_items, L, static_cast<WsHeader *>(d_ws));
+    ka_status s = cuda_status(cudaGetLastError());
+    if (s != KA_OK) return s;
+    const unsigned grid = unsigned(device_info().sm_count) * 8;
+    k_generate_batch<<<grid, kGenBlock, 0, st>>>(d_items, n_items, L.tile_off);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // extern "C"

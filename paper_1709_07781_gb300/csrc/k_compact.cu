@@ -1,23 +1,12 @@
 // Fused single-pass stream compaction (Sec. 4.1's flag, prefix-sum and move
 // phases in one kernel; the paper's own OpenCL version fuses only the last
 // two, and Sec. 3.6 names "several kernels inside one actor" as the way to
-// avoid inter-stage traffic).
-//
-// One tile = BLOCK threads x IPT entries. Per tile:
-//   1. 16-byte streaming loads in row-major stripes (row r, thread t holds
-//      entries [4 (r BLOCK + t), +4)), so every warp load is fully coalesced;
-//   2. the keep-test gives a 4-bit mask per row; per-row counts are packed
-//      into one 32-bit word (8 bits per row, at most 128 per warp) and scanned
-//      across the warp with five shuffles for all rows at once;
-//   3. warp 0 scans the per-warp totals (16-bit fields), publishes the tile's
-//      count and runs the decoupled look-back for the tile's output offset;
-//   4. kept entries go to shared memory at their tile-local offset, then the
-//      block writes the contiguous run out[offset, offset + count) with
-//      consecutive threads on consecutive words.
+// avoid inter-stage traffic). The per-tile work is compact_tile (ka_tile.cuh).
 // Blocks are persistent (grid = resident blocks) and take tiles by ticket.
 // Output offsets never exceed input positions, so out == in is safe: a tile
 // writes only after all its predecessors have loaded their input.
 #include "ka_internal.h"
+#include "ka_tile.cuh"
 
 namespace ka {
 
@@ -38,20 +27,9 @@ struct CompactArgs {
 template <int BLOCK, int IPT>
 __global__ void __launch_bounds__(BLOCK) k_compact_fused(const CompactArgs a) {
     constexpr int T = BLOCK * IPT;
-    constexpr int ROWS = IPT / 4;
-    constexpr int WARPS = BLOCK / 32;
-    static_assert(ROWS >= 1 && ROWS <= 4, "8-bit row fields hold at most 4 rows");
-    static_assert(WARPS <= 16, "16-bit block fields hold at most 16 warps x 128");
-
-    __shared__ uint32_t s_out[T];
-    __shared__ uint32_t s_wtot[WARPS];
-    __shared__ uint64_t s_wexcl[WARPS];
-    __shared__ uint64_t s_tot;
-    __shared__ uint32_t s_ticket, s_epoch, s_prefix, s_n, s_err, s_spin;
-
+    __shared__ CompactSmem<BLOCK, IPT> sm;
+    __shared__ uint32_t s_ticket, s_epoch, s_n, s_spin;
     const int tid = threadIdx.x;
-    const int lane = tid & 31;
-    const int warp = tid >> 5;
 
     if (tid == 0) {
         uint32_t n = a.n;
@@ -65,6 +43,7 @@ __global__ void __launch_bounds__(BLOCK) k_compact_fused(const CompactArgs a) {
     }
     __syncthreads();
     const uint32_t n = s_n;
+    const uint32_t spin = s_spin;
     const uint32_t live_tiles = uint32_t((uint64_t(n) + T - 1) / T);
     if (live_tiles > a.status_cap) {
         if (tid == 0 && blockIdx.x == 0) record_error(a.ws, kDevErrWorkspace, 0);
@@ -86,89 +65,8 @@ __global__ void __launch_bounds__(BLOCK) k_compact_fused(const CompactArgs a) {
         if (tile >= live_tiles) break;
         const uint32_t base = tile * uint32_t(T);
         const uint32_t valid = (n - base) < uint32_t(T) ? (n - base) : uint32_t(T);
-
-        uint32_t v[ROWS][4];
-        uint32_t m[ROWS];
-        if (valid == uint32_t(T) && a.vec_ok) {
-#pragma unroll
-            for (int r = 0; r < ROWS; ++r) {
-                const uint4 q = ld_stream_v4(a.in + base + (r * BLOCK + tid) * 4);
-                v[r][0] = q.x * a.mul;
-                v[r][1] = q.y * a.mul;
-                v[r][2] = q.z * a.mul;
-                v[r][3] = q.w * a.mul;
-            }
-        } else {
-#pragma unroll
-            for (int r = 0; r < ROWS; ++r) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const uint32_t idx = uint32_t(r * BLOCK + tid) * 4 + j;
-                    v[r][j] = idx < valid ? ld_stream_u32(a.in + base + idx) * a.mul : 0u;
-                }
-            }
-        }
-        uint32_t packed = 0;
-#pragma unroll
-        for (int r = 0; r < ROWS; ++r) {
-            uint32_t mk = pred_mask4(a.pred, v[r][0], v[r][1], v[r][2], v[r][3]);
-            if (valid != uint32_t(T)) {
-                const uint32_t idx0 = uint32_t(r * BLOCK + tid) * 4;
-                const uint32_t left = valid > idx0 ? valid - idx0 : 0u;
-                mk &= left >= 4 ? 0xFu : ((1u << left) - 1u);
-            }
-            m[r] = mk;
-            packed += __popc(mk) << (8 * r);
-        }
-        const uint32_t incl = warp_incl_scan(packed, lane);
-        const uint32_t lane_excl = incl - packed;
-        if (lane == 31) s_wtot[warp] = incl;
-        __syncthreads();
-
-        if (warp == 0) {
-            const uint64_t wt = lane < WARPS ? spread8to16(s_wtot[lane]) : 0ull;
-            const uint64_t wincl = warp_incl_scan64(wt, lane, WARPS);
-            if (lane < WARPS) s_wexcl[lane] = wincl - wt;
-            const uint64_t tot = __shfl_sync(kFull, wincl, WARPS - 1);
-            const uint32_t agg = uint32_t(tot & 0xFFFFu) + uint32_t((tot >> 16) & 0xFFFFu) +
-                                 uint32_t((tot >> 32) & 0xFFFFu) + uint32_t(tot >> 48);
-            bool err;
-            const uint32_t prefix = lookback_warp(a.status, tile, 0u, epoch, agg, s_spin, a.ws, &err);
-            if (lane == 0) {
-                s_tot = tot;
-                s_prefix = prefix;
-                s_err = err ? 1u : 0u;
-                if (!err && tile == live_tiles - 1) *a.count = prefix + agg;
-            }
-        }
-        __syncthreads();
-        const uint64_t tot = s_tot;
-        const uint32_t prefix = s_prefix;
-        const bool err = s_err != 0u;
-        if (!err) {
-            const uint64_t wex = s_wexcl[warp];
-            uint32_t rowbase = 0;
-#pragma unroll
-            for (int r = 0; r < ROWS; ++r) {
-                uint32_t off = rowbase + uint32_t((wex >> (16 * r)) & 0xFFFFu) + ((lane_excl >> (8 * r)) & 0xFFu);
-                const uint32_t mk = m[r];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if ((mk >> j) & 1u) {
-                        s_out[off] = v[r][j];
-                        ++off;
-                    }
-                }
-                rowbase += uint32_t((tot >> (16 * r)) & 0xFFFFu);
-            }
-        }
-        __syncthreads();
-        if (!err) {
-            const uint32_t agg = uint32_t(tot & 0xFFFFu) + uint32_t((tot >> 16) & 0xFFFFu) +
-                                 uint32_t((tot >> 32) & 0xFFFFu) + uint32_t(tot >> 48);
-            uint32_t *dst = a.out + prefix;
-            for (uint32_t k = tid; k < agg; k += BLOCK) dst[k] = s_out[k];
-        }
+        compact_tile<BLOCK, IPT>(sm, a.in + base, a.out, valid, a.vec_ok != 0u, a.mul, a.pred, a.status, tile, 0u,
+                                 epoch, spin, a.ws, tile == live_tiles - 1 ? a.count : nullptr);
     }
 }
 

@@ -118,6 +118,54 @@ __host__ __device__ __forceinline__ uint32_t popc32(uint32_t x) {
 #endif
 }
 
+// Inverse of an odd d modulo 2^32 by Newton iteration: x <- x (2 - d x)
+// doubles the number of correct low bits each step, starting from x = d
+// (correct to 3 bits for odd d).
+__host__ __device__ inline uint32_t inverse_odd(uint32_t d) {
+    uint32_t x = d;
+    for (int i = 0; i < 5; ++i) x *= 2u - d * x;
+    return x;
+}
+
+// Canonical predicate for an API (kind, param): 0 on success, -1 for an
+// unknown kind or a zero modulus. Kind numbers are those of ka_pred_kind.
+__host__ __device__ inline int pred_canon(int32_t kind, uint32_t param, PredDev *out) {
+    PredDev p{};
+    switch (kind) {
+    case 0: p.kind = kAndMaskEq0; p.a = param; break;  // KA_PRED_AND_MASK_EQ0
+    case 1: p.kind = kLt; p.a = param; break;          // KA_PRED_LT
+    case 2:                                            // KA_PRED_TOPBITS_LT
+        // (x >> 28) < p  <=>  x < p * 2^28 for p <= 15; every x passes for p >= 16.
+        if (param >= 16u) {
+            p.kind = kAll;
+        } else {
+            p.kind = kLt;
+            p.a = param << 28;
+        }
+        break;
+    case 3: p.kind = kPopcOdd; break;                  // KA_PRED_POPC_ODD
+    case 4: {                                          // KA_PRED_MOD_NE0
+        if (param == 0u) return -1;
+        uint32_t shift = 0, odd = param;
+        while ((odd & 1u) == 0u) {
+            odd >>= 1;
+            ++shift;
+        }
+        p.kind = kModNe0;
+        p.a = inverse_odd(odd);
+        p.b = 0xFFFFFFFFu / odd;
+        p.c = shift == 0 ? 0u : (0xFFFFFFFFu >> (32 - shift));
+        p.d = shift;
+        break;
+    }
+    case 5: p.kind = kNe; p.a = param; break;          // KA_PRED_NE
+    case 6: p.kind = kAll; break;                      // KA_PRED_ALL
+    default: return -1;
+    }
+    *out = p;
+    return 0;
+}
+
 template <int K>
 __host__ __device__ __forceinline__ bool keep_k(const PredDev &p, uint32_t x) {
     if (K == kAndMaskEq0) return (x & p.a) == 0u;

@@ -3,12 +3,6 @@
 
 extern "C" {
 
-ka_status ka_batch_workspace_size(uint32_t, uint64_t, const ka_tile *, uint64_t *) { return KA_E_UNSUPPORTED; }
-ka_status ka_compact_batch(const ka_batch_item *, uint32_t, uint64_t, void *, uint64_t, const ka_tile *, uint32_t,
-                           void *) {
-    return KA_E_UNSUPPORTED;
-}
-ka_status ka_generate_batch(const ka_gen_item *, uint32_t, void *, uint64_t, void *) { return KA_E_UNSUPPORTED; }
 ka_status ka_system_create(const ka_config *, ka_system **) { return KA_E_UNSUPPORTED; }
 ka_status ka_system_destroy(ka_system *, int32_t) { return KA_E_UNSUPPORTED; }
 ka_status ka_system_pool_bytes(ka_system *, uint64_t *, uint64_t *) { return KA_E_UNSUPPORTED; }

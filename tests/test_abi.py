@@ -15,8 +15,8 @@ HEADER = os.path.join(ROOT, "include", "ka.h")
 
 @pytest.fixture(scope="module")
 def ka():
-    from paper_1709_07781_gb300 import build as kb
-    kb.build()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_1709_07781_gb300 as m
     return m
 
