@@ -28,7 +28,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libka_oracle.so")
 
 # The oracle's own predicate numbering (see ka_oracle.c).
-PRED_IDS = {"and_mask_eq0": 0, "lt": 1, "topbits_lt": 2, "popc_odd": 3, "mod_ne0": 4, "ne": 5}
+PRED_IDS = {"and_mask_eq0": 0, "lt": 1, "topbits_lt": 2, "popc_odd": 3, "mod_ne0": 4, "ne": 5, "all": 6}
 
 _lib = None
 _lock = threading.Lock()

@@ -33,7 +33,8 @@ enum {
     ORA_TOPBITS_LT = 2,   /* keep (x >> 28) < param         */
     ORA_POPC_ODD = 3,     /* keep popcount(x) odd           */
     ORA_MOD_NE0 = 4,      /* keep x mod param != 0          */
-    ORA_NE = 5            /* keep x != param (remove value) */
+    ORA_NE = 5,           /* keep x != param (remove value) */
+    ORA_ALL = 6           /* keep every entry (a map stage)  */
 };
 
 /* SplitMix64: the (i+1)-th output of the sequential generator whose 64-bit
@@ -73,6 +74,7 @@ int ora_keep(int kind, uint32_t param, uint32_t x)
     case ORA_POPC_ODD:     return ora_popcount(x) % 2 == 1;
     case ORA_MOD_NE0:      return param == 0u ? -1 : (x % param) != 0u;
     case ORA_NE:           return x != param;
+    case ORA_ALL:          return 1;
     default:               return -1;
     }
 }

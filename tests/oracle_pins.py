@@ -62,6 +62,8 @@ def numpy_keep(pred, param, x):
         return (x % np.uint32(param)) != 0
     if pred == "ne":
         return x != np.uint32(param)
+    if pred == "all":
+        return np.ones(x.shape, dtype=bool)
     raise ValueError(pred)
 
 
@@ -77,6 +79,7 @@ def check_predicate_values():
         ("mod_ne0", 3, 9, 0), ("mod_ne0", 3, 10, 1), ("mod_ne0", 3, 0, 0), ("mod_ne0", 3, 0xFFFFFFFF, 0),
         ("mod_ne0", 3, 0xFFFFFFFE, 1), ("mod_ne0", 7, 49, 0),
         ("ne", 0, 0, 1 - 1), ("ne", 0, 5, 1), ("ne", 5, 5, 0),
+        ("all", 0, 0, 1), ("all", 0, 0xFFFFFFFF, 1), ("all", 7, 7, 1),
     ]
     for pred, param, x, want in cases:
         got = oracle.keep(pred, param, x)
@@ -143,7 +146,7 @@ def _is_stable_subsequence(y, x):
 def check_compaction_library(n=20000, seed=11):
     x = ki.uniform_u32(seed, n)
     for pred, param in [("and_mask_eq0", 3), ("lt", ki.threshold_for(0.5)), ("topbits_lt", 8),
-                        ("popc_odd", 0), ("mod_ne0", 3), ("ne", int(x[17]))]:
+                        ("popc_odd", 0), ("mod_ne0", 3), ("ne", int(x[17])), ("all", 0)]:
         mask = numpy_keep(pred, param, x)
         y, k = oracle.compact(x, pred, param)
         assert k == int(mask.sum())

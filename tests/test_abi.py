@@ -75,7 +75,7 @@ def test_kernel_predicates_match_the_oracle_definition(ka):
     import ka_inputs as ki
     xs = list(map(int, ki.uniform_u32(5, 3000))) + [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 12, 0x7FFFFFFF, 0x80000000,
                                                    0xFFFFFFFF, 0xFFFFFFFE, 0xFFFFFFFD, 0xFFFFFFFC, 3 * 1431655765]
-    cases = [("and_mask_eq0", 3), ("lt", 12345), ("popc_odd", 0), ("ne", 7), ("ne", 0)]
+    cases = [("and_mask_eq0", 3), ("lt", 12345), ("popc_odd", 0), ("ne", 7), ("ne", 0), ("all", 0)]
     cases += [("topbits_lt", p) for p in (0, 1, 7, 8, 15, 16, 100)]
     cases += [("mod_ne0", d) for d in (1, 2, 3, 4, 5, 6, 7, 12, 24, 96, 1000, 65536, 2**31, 2**31 + 1,
                                        0xFFFFFFFF, 0xFFFFFFFE)]

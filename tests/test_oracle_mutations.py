@@ -27,6 +27,7 @@ MUTATIONS = {
     "mask_inverted": ("(x & param) == 0u", "(x & param) != 0u"),
     "interleave_swapped": ("index[2 * i] = chunk_ids[i];\n        index[2 * i + 1] = literals[i];",
                            "index[2 * i] = literals[i];\n        index[2 * i + 1] = chunk_ids[i];"),
+    "all_drops_everything": ("case ORA_ALL:          return 1;", "case ORA_ALL:          return 0;"),
     "scatter_off_by_one": ("y[o[i]] = x[i];", "y[o[i] + (o[i] > 0)] = x[i];"),
 }
 
