@@ -93,7 +93,8 @@ typedef enum ka_pred_kind {
 #define KA_XFORM_HASH 1u      /* x -> x * 2654435761 mod 2^32 */
 
 /* Tile shape of a tiled kernel: threads per block and items per thread.
- * block in {128, 256, 512}, ipt in {4, 8, 16}, block * ipt <= 4096.
+ * Supported: block 128, 256 or 512 with ipt 4, 8 or 16, and block 1024 with
+ * ipt 4 or 8 (so a tile holds 512 to 8192 entries).
  * A NULL tile, or {0, 0}, picks the library default (or the autotuned shape
  * once ka_autotune has run for that kernel). */
 typedef struct ka_tile {

@@ -303,3 +303,137 @@ def ka_debug_pred_keep(pred: int, param: int, x: int):
 
 def ka_autotune_load(cache_path: str) -> int:
     return lib.ka_autotune_load(cache_path.encode())
+
+
+# ---------------------------------------------------------------------------
+# Actor layer (handles are opaque ints).
+# ---------------------------------------------------------------------------
+def ka_system_create(device: int = 0, stream=None, budget_bytes: int = 0, autotune_cache=None, debug: int = 0):
+    cfg = ka_config(device, debug, stream_ptr(stream), budget_bytes,
+                    autotune_cache.encode() if autotune_cache else None)
+    h = c_vp(None)
+    s = lib.ka_system_create(ctypes.byref(cfg), ctypes.byref(h))
+    return s, h.value
+
+
+def ka_system_destroy(sys_h, force: int = 0) -> int:
+    return lib.ka_system_destroy(sys_h, force)
+
+
+def ka_system_pool_bytes(sys_h):
+    a, b = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    s = lib.ka_system_pool_bytes(sys_h, ctypes.byref(a), ctypes.byref(b))
+    return s, a.value, b.value
+
+
+def ka_ref_wrap(sys_h, d_ptr, n: int, capacity: int, dtype: int = KA_U32, access: int = KA_READ_WRITE):
+    h = c_vp(None)
+    s = lib.ka_ref_wrap(sys_h, ptr(d_ptr), n, capacity, dtype, access, ctypes.byref(h))
+    return s, h.value
+
+
+def ka_ref_alloc(sys_h, capacity: int, dtype: int = KA_U32):
+    h = c_vp(None)
+    s = lib.ka_ref_alloc(sys_h, capacity, dtype, ctypes.byref(h))
+    return s, h.value
+
+
+def ka_ref_count(ref_h):
+    n = ctypes.c_uint64(0)
+    s = lib.ka_ref_count(ref_h, ctypes.byref(n))
+    return s, n.value
+
+
+def ka_ref_info(ref_h):
+    p, cap, dt, acc = c_vp(None), ctypes.c_uint64(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    s = lib.ka_ref_info(ref_h, ctypes.byref(p), ctypes.byref(cap), ctypes.byref(dt), ctypes.byref(acc))
+    return s, p.value, cap.value, dt.value, acc.value
+
+
+def ka_ref_retain(ref_h) -> int:
+    return lib.ka_ref_retain(ref_h)
+
+
+def ka_ref_release(ref_h) -> int:
+    return lib.ka_ref_release(ref_h)
+
+
+def ka_ref_serialize(ref_h, cap: int = 64):
+    buf = ctypes.create_string_buffer(cap)
+    n = ctypes.c_uint64(0)
+    return lib.ka_ref_serialize(ref_h, buf, cap, ctypes.byref(n)), n.value
+
+
+def ka_spawn_stage(sys_h, kind: int, pred: int = 0, param: int = 0, xform: int = 0, tile=(0, 0)):
+    d = ka_stage_desc(kind, pred, param, xform, ka_tile(int(tile[0]), int(tile[1])))
+    h = c_vp(None)
+    s = lib.ka_spawn_stage(sys_h, ctypes.byref(d), ctypes.byref(h))
+    return s, h.value
+
+
+def ka_compose(b_h, a_h):
+    h = c_vp(None)
+    s = lib.ka_compose(b_h, a_h, ctypes.byref(h))
+    return s, h.value
+
+
+def ka_actor_arity(actor_h):
+    i, o = ctypes.c_int32(0), ctypes.c_int32(0)
+    s = lib.ka_actor_arity(actor_h, ctypes.byref(i), ctypes.byref(o))
+    return s, i.value, o.value
+
+
+def ka_actor_release(actor_h) -> int:
+    return lib.ka_actor_release(actor_h)
+
+
+def make_msg(refs=(), h_in=None, h_n: int = 0, h_out=None, h_out_cap: int = 0, seed: int = 0, gen_n: int = 0):
+    """ka_msg for ka_request: device refs and/or host buffers (numpy uint32)."""
+    m = ka_msg()
+    m.n_refs = len(refs)
+    for i, r in enumerate(refs):
+        m.refs[i] = r
+    if h_in is not None:
+        m.h_in = h_in.ctypes.data_as(c_u32p)
+        m.h_n = h_n if h_n else h_in.size
+    if h_out is not None:
+        m.h_out = h_out.ctypes.data_as(c_u32p)
+        m.h_out_cap = h_out_cap if h_out_cap else h_out.size
+    m.seed = seed & (2**64 - 1)
+    m.gen_n = gen_n
+    return m
+
+
+def ka_request(actor_h, msg: ka_msg):
+    h = c_vp(None)
+    s = lib.ka_request(actor_h, ctypes.byref(msg), ctypes.byref(h))
+    return s, h.value
+
+
+def ka_receive(req_h, timeout_ns: int = -1):
+    """Returns (status, msg): msg.refs[:msg.n_refs] are result ref handles."""
+    m = ka_msg()
+    s = lib.ka_receive(req_h, timeout_ns, ctypes.byref(m))
+    return s, m
+
+
+def ka_debug_fail_stage(actor_h, fail_after: int) -> int:
+    return lib.ka_debug_fail_stage(actor_h, fail_after)
+
+
+def ka_debug_kill_dispatcher(sys_h) -> int:
+    return lib.ka_debug_kill_dispatcher(sys_h)
+
+
+def ka_system_monitor(sys_h, fn, user=None) -> int:
+    """fn(user, reason) is called once when the dispatcher dies; keep `fn` (a
+    MONITOR_FN) alive while the system exists."""
+    return lib.ka_system_monitor(sys_h, fn, user)
+
+
+def ka_actor_enable_graph(actor_h, enable: int = 1) -> int:
+    return lib.ka_actor_enable_graph(actor_h, enable)
+
+
+def ka_serve_run(sys_h, reqs, n_reqs: int, opt, results, stats) -> int:
+    return lib.ka_serve_run(sys_h, reqs, n_reqs, ctypes.byref(opt), results, ctypes.byref(stats))

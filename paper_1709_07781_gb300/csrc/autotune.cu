@@ -26,7 +26,11 @@ int bucket_of(uint64_t n) {
     return b;
 }
 
-const ka_tile kShapes[] = {{128, 4}, {128, 8}, {128, 16}, {256, 4}, {256, 8}, {256, 16}, {512, 4}, {512, 8}};
+const ka_tile kShapes[] = {
+#define KA_SHAPE(B, I) {B, I},
+    KA_FOR_EACH_SHAPE(KA_SHAPE)
+#undef KA_SHAPE
+};
 
 ka_tile default_tile(int32_t kernel, uint64_t n) {
     (void)kernel;

@@ -38,9 +38,11 @@ ka_status make_pred(int32_t kind, uint32_t param, PredDev *out) {
 }
 
 bool tile_supported(uint32_t block, uint32_t ipt) {
-    if (!(block == 128 || block == 256 || block == 512)) return false;
-    if (!(ipt == 4 || ipt == 8 || ipt == 16)) return false;
-    return block * ipt <= 4096;
+#define KA_SUPPORTED(B, I) \
+    if (block == B && ipt == I) return true;
+    KA_FOR_EACH_SHAPE(KA_SUPPORTED)
+#undef KA_SUPPORTED
+    return false;
 }
 
 ka_status check_workspace(const void *ws, uint64_t ws_bytes, uint64_t tiles_needed) {

@@ -306,15 +306,11 @@ ka_status ka_compact_batch(const ka_batch_item *d_items, uint32_t n_items, uint3
     k_batch_plan<<<1, kPlanBlock, 0, st>>>(d_items, n_items, t.block * t.ipt, a.L, a.ws);
     ka_status s = cuda_status(cudaGetLastError());
     if (s != KA_OK) return s;
-    switch (t.block * 100 + t.ipt) {
-    case 12804: return launch_batch_shape<128, 4>(a, grid, st);
-    case 12808: return launch_batch_shape<128, 8>(a, grid, st);
-    case 12816: return launch_batch_shape<128, 16>(a, grid, st);
-    case 25604: return launch_batch_shape<256, 4>(a, grid, st);
-    case 25608: return launch_batch_shape<256, 8>(a, grid, st);
-    case 25616: return launch_batch_shape<256, 16>(a, grid, st);
-    case 51204: return launch_batch_shape<512, 4>(a, grid, st);
-    case 51208: return launch_batch_shape<512, 8>(a, grid, st);
+    switch (shape_key(t.block, t.ipt)) {
+#define KA_CASE(B, I) \
+    case shape_key(B, I): return launch_batch_shape<B, I>(a, grid, st);
+        KA_FOR_EACH_SHAPE(KA_CASE)
+#undef KA_CASE
     default: return KA_E_ARG;
     }
 }

@@ -110,15 +110,11 @@ ka_status launch_compact(const CompactLaunch &L, cudaStream_t stream) {
     a.mul = L.mul;
     a.vec_ok = (reinterpret_cast<uintptr_t>(L.in) & 15u) == 0 ? 1u : 0u;
     a.pred = L.pred;
-    switch (t.block * 100 + t.ipt) {
-    case 12804: return launch_shape<128, 4>(a, L.n, stream);
-    case 12808: return launch_shape<128, 8>(a, L.n, stream);
-    case 12816: return launch_shape<128, 16>(a, L.n, stream);
-    case 25604: return launch_shape<256, 4>(a, L.n, stream);
-    case 25608: return launch_shape<256, 8>(a, L.n, stream);
-    case 25616: return launch_shape<256, 16>(a, L.n, stream);
-    case 51204: return launch_shape<512, 4>(a, L.n, stream);
-    case 51208: return launch_shape<512, 8>(a, L.n, stream);
+    switch (shape_key(t.block, t.ipt)) {
+#define KA_CASE(B, I) \
+    case shape_key(B, I): return launch_shape<B, I>(a, L.n, stream);
+        KA_FOR_EACH_SHAPE(KA_CASE)
+#undef KA_CASE
     default: return KA_E_ARG;
     }
 }

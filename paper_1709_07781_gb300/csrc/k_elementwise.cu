@@ -163,6 +163,14 @@ ka_status launch_copy_count(const uint32_t *n_ptr, uint64_t n, uint32_t *n_out, 
     return cuda_status(cudaGetLastError());
 }
 
+// The empty stage: one launch that does no work (prices a message-passing stage).
+__global__ void k_empty() {}
+
+ka_status launch_empty(cudaStream_t stream) {
+    k_empty<<<1, 32, 0, stream>>>();
+    return cuda_status(cudaGetLastError());
+}
+
 }  // namespace ka
 
 using namespace ka;

@@ -182,15 +182,11 @@ ka_status launch_exclusive_scan(const uint32_t *in, uint64_t n, const uint32_t *
     const uint64_t cap_words = (ws_bytes - kWsHeaderBytes) / 8;
     a.status_cap = cap_words > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(cap_words);
     a.vec_ok = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) == 0 ? 1u : 0u;
-    switch (t.block * 100 + t.ipt) {
-    case 12804: return launch_scan_shape<128, 4>(a, n, stream);
-    case 12808: return launch_scan_shape<128, 8>(a, n, stream);
-    case 12816: return launch_scan_shape<128, 16>(a, n, stream);
-    case 25604: return launch_scan_shape<256, 4>(a, n, stream);
-    case 25608: return launch_scan_shape<256, 8>(a, n, stream);
-    case 25616: return launch_scan_shape<256, 16>(a, n, stream);
-    case 51204: return launch_scan_shape<512, 4>(a, n, stream);
-    case 51208: return launch_scan_shape<512, 8>(a, n, stream);
+    switch (shape_key(t.block, t.ipt)) {
+#define KA_CASE(B, I) \
+    case shape_key(B, I): return launch_scan_shape<B, I>(a, n, stream);
+        KA_FOR_EACH_SHAPE(KA_CASE)
+#undef KA_CASE
     default: return KA_E_ARG;
     }
 }

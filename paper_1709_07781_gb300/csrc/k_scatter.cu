@@ -18,6 +18,7 @@ struct ScatterArgs {
     const uint32_t *o;
     const uint32_t *n_ptr;
     uint32_t *out;
+    uint32_t *count_out;  // optional: receives the result length o[n-1] + f[n-1]
     uint32_t n;
     uint32_t vec_ok;
 };
@@ -35,12 +36,15 @@ __global__ void __launch_bounds__(kScatterBlock) k_scatter(const ScatterArgs a) 
         n = d < n ? d : n;
     }
     const uint32_t live_tiles = uint32_t((uint64_t(n) + T - 1) / T);
+    if (a.count_out && blockIdx.x == 0 && tid == 0 && live_tiles == 0) *a.count_out = 0u;
     for (uint32_t tile = blockIdx.x; tile < live_tiles; tile += gridDim.x) {
         const uint32_t base = tile * uint32_t(T);
         const uint32_t valid = (n - base) < uint32_t(T) ? (n - base) : uint32_t(T);
         const uint32_t last = base + valid - 1;
         const uint32_t o0 = a.o[base];
-        uint32_t kept = a.o[last] + (a.f[last] ? 1u : 0u) - o0;
+        const uint32_t end = a.o[last] + (a.f[last] ? 1u : 0u);
+        if (a.count_out && tid == 0 && tile == live_tiles - 1) *a.count_out = end;
+        uint32_t kept = end - o0;
         if (kept > valid) kept = valid;  // only if flags/offsets are inconsistent
         if (valid == uint32_t(T) && a.vec_ok) {
 #pragma unroll
@@ -79,16 +83,18 @@ __global__ void __launch_bounds__(kScatterBlock) k_scatter(const ScatterArgs a) 
 }
 
 ka_status launch_scatter(const uint32_t *x, const uint32_t *flags, const uint32_t *offsets, uint64_t n,
-                         const uint32_t *n_ptr, uint32_t *out, cudaStream_t stream) {
+                         const uint32_t *n_ptr, uint32_t *out, uint32_t *count_out, cudaStream_t stream) {
     if (n > 0xFFFFFFFFull) return KA_E_ARG;
     if (n && (!x || !flags || !offsets || !out)) return KA_E_ARG;
-    if (n == 0) return KA_OK;
+    if (count_out && count_out == n_ptr) return KA_E_ARG;
+    if (n == 0 && !count_out) return KA_OK;
     ScatterArgs a;
     a.x = x;
     a.f = flags;
     a.o = offsets;
     a.n_ptr = n_ptr;
     a.out = out;
+    a.count_out = count_out;
     a.n = uint32_t(n);
     a.vec_ok = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(flags) |
                  reinterpret_cast<uintptr_t>(offsets)) & 15u) == 0 ? 1u : 0u;
@@ -102,6 +108,7 @@ ka_status launch_scatter(const uint32_t *x, const uint32_t *flags, const uint32_
     uint64_t grid = (n + T - 1) / T;
     const uint64_t resident = uint64_t(device_info().sm_count) * occupancy;
     if (grid > resident) grid = resident;
+    if (grid < 1) grid = 1;
     k_scatter<<<unsigned(grid), kScatterBlock, 0, stream>>>(a);
     return cuda_status(cudaGetLastError());
 }
@@ -112,5 +119,5 @@ using namespace ka;
 
 extern "C" ka_status ka_scatter(const uint32_t *d_x, const uint32_t *d_flags, const uint32_t *d_offsets, uint64_t n,
                                 const uint32_t *d_n, uint32_t *d_out, void *stream) {
-    return launch_scatter(d_x, d_flags, d_offsets, n, d_n, d_out, static_cast<cudaStream_t>(stream));
+    return launch_scatter(d_x, d_flags, d_offsets, n, d_n, d_out, nullptr, static_cast<cudaStream_t>(stream));
 }

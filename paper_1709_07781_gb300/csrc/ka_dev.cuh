@@ -249,13 +249,20 @@ __device__ __forceinline__ uint64_t spread8to16(uint32_t x) {
 // Decoupled look-back, run by one full warp for tile `tile` whose first tile
 // of its segment is `first_tile` (0 for a single array; the first tile of
 // an instance in a batch). Publishes the tile's aggregate (or, for the first
-// tile, its inclusive prefix), walks back 32 predecessors at a time, then
+// tile, its inclusive prefix), walks back over its predecessors, then
 // publishes the inclusive prefix. Returns the exclusive prefix of the tile.
-// Every poll loop is bounded by `spin_limit`; on time-out, or when a
-// predecessor reports an error, the tile publishes the error flag (so its
-// successors stop at once), the first error is recorded in the workspace
-// header, and *err is set.
+//
+// Each poll issues kLookbackWindows independent loads per lane, so one L2
+// round trip examines 32 * kLookbackWindows predecessors; windows are then
+// consumed nearest first until an inclusive prefix is met, and a window with
+// a not-yet-published word is polled again (keeping the sum of the windows
+// already consumed). Every poll loop is bounded by `spin_limit`; on time-out,
+// or when a predecessor reports an error, the tile publishes the error flag
+// (so its successors stop at once), the first error is recorded in the
+// workspace header, and *err is set.
 // ---------------------------------------------------------------------------
+constexpr int kLookbackWindows = 4;
+
 __device__ __forceinline__ uint32_t lookback_warp(uint64_t *status, uint32_t tile, uint32_t first_tile,
                                                   uint32_t epoch, uint32_t aggregate, uint32_t spin_limit,
                                                   WsHeader *ws, bool *err) {
@@ -267,22 +274,45 @@ __device__ __forceinline__ uint32_t lookback_warp(uint64_t *status, uint32_t til
     }
     if (lane == 0) st_relaxed_u64(status + tile, pack_status(epoch, kFlagAggregate, aggregate));
     uint32_t exclusive = 0;
-    bool failed = false;
-    int64_t window = int64_t(tile) - 1;
+    bool failed = false, done = false;
+    int64_t window = int64_t(tile) - 1;  // nearest predecessor not yet summed
     const uint32_t want_epoch = epoch & kEpochMask;
-    for (;;) {
-        const int64_t idx = window - lane;
-        uint32_t flag = kFlagInclusive, value = 0;
-        uint32_t polls = 0, sleep_ns = 0;
-        for (;;) {
+    uint32_t polls = 0, sleep_ns = 0;
+    while (!done) {
+        uint32_t flag[kLookbackWindows], value[kLookbackWindows];
+#pragma unroll
+        for (int j = 0; j < kLookbackWindows; ++j) {
+            const int64_t idx = window - 32 * j - lane;
+            flag[j] = kFlagInclusive;
+            value[j] = 0;
             if (idx >= int64_t(first_tile)) {
                 const uint64_t s = ld_relaxed_u64(status + idx);
-                flag = uint32_t(s >> 34) == want_epoch ? uint32_t(s >> 32) & 3u : kFlagInvalid;
-                value = uint32_t(s);
+                flag[j] = uint32_t(s >> 34) == want_epoch ? uint32_t(s >> 32) & 3u : kFlagInvalid;
+                value[j] = uint32_t(s);
             }
-            if (__all_sync(kFull, flag != kFlagInvalid)) break;
+        }
+        int consumed = 0;
+#pragma unroll
+        for (int j = 0; j < kLookbackWindows; ++j) {
+            if (done || consumed != j) continue;
+            if (!__all_sync(kFull, flag[j] != kFlagInvalid)) continue;
+            const uint32_t stop = __ballot_sync(kFull, flag[j] >= kFlagInclusive);
+            if (stop) {
+                const int first = __ffs(stop) - 1;
+                exclusive += warp_sum(lane <= first ? value[j] : 0u);
+                failed = __shfl_sync(kFull, flag[j], first) == kFlagError;
+                done = true;
+            } else {
+                exclusive += warp_sum(value[j]);
+                ++consumed;
+            }
+        }
+        if (done) break;
+        window -= 32 * consumed;
+        if (consumed == 0) {
             if (++polls >= spin_limit) {
                 failed = true;
+                if (lane == 0) record_error(ws, kDevErrTimeout, tile);
                 break;
             }
             if (polls > 8) {
@@ -290,19 +320,6 @@ __device__ __forceinline__ uint32_t lookback_warp(uint64_t *status, uint32_t til
                 sleep_ns = sleep_ns < 256 ? sleep_ns * 2 + 32 : 256;
             }
         }
-        if (failed) {
-            if (lane == 0) record_error(ws, kDevErrTimeout, tile);
-            break;
-        }
-        const uint32_t stop = __ballot_sync(kFull, flag >= kFlagInclusive);
-        if (stop) {
-            const int first = __ffs(stop) - 1;
-            exclusive += warp_sum(lane <= first ? value : 0u);
-            failed = __shfl_sync(kFull, flag, first) == kFlagError;
-            break;
-        }
-        exclusive += warp_sum(value);
-        window -= 32;
     }
     if (lane == 0)
         st_relaxed_u64(status + tile,

@@ -24,7 +24,11 @@ ka_status cuda_status(cudaError_t e);
 // or a zero modulus.
 ka_status make_pred(int32_t kind, uint32_t param, PredDev *out);
 
-// Supported tile shapes.
+// Supported tile shapes (block threads, items per thread); the list drives
+// every templated launcher through KA_FOR_EACH_SHAPE(X), X(block, ipt).
+#define KA_FOR_EACH_SHAPE(X) \
+    X(128, 4) X(128, 8) X(128, 16) X(256, 4) X(256, 8) X(256, 16) X(512, 4) X(512, 8) X(512, 16) X(1024, 4) X(1024, 8)
+constexpr uint32_t shape_key(uint32_t block, uint32_t ipt) { return block * 100 + ipt; }
 bool tile_supported(uint32_t block, uint32_t ipt);
 // Shape to use for `kernel` at size n: explicit shape, else autotuned, else default.
 ka_tile resolve_tile(int32_t kernel, uint64_t n, const ka_tile *requested);
@@ -55,7 +59,8 @@ ka_status launch_exclusive_scan(const uint32_t *in, uint64_t n, const uint32_t *
                                 uint32_t *total, void *ws, uint64_t ws_bytes, ka_tile tile,
                                 cudaStream_t stream);
 ka_status launch_scatter(const uint32_t *x, const uint32_t *flags, const uint32_t *offsets, uint64_t n,
-                         const uint32_t *n_ptr, uint32_t *out, cudaStream_t stream);
+                         const uint32_t *n_ptr, uint32_t *out, uint32_t *count_out, cudaStream_t stream);
+ka_status launch_empty(cudaStream_t stream);
 ka_status launch_generate(uint32_t *out, uint64_t n, uint64_t seed, uint32_t *n_out, cudaStream_t stream);
 ka_status launch_map_hash(const uint32_t *in, uint64_t n, const uint32_t *n_ptr, uint32_t *out,
                           uint32_t *n_out, cudaStream_t stream);

@@ -50,7 +50,7 @@ __device__ __forceinline__ void compact_tile(CompactSmem<BLOCK, IPT> &sm, const 
     constexpr int ROWS = IPT / 4;
     constexpr int WARPS = BLOCK / 32;
     static_assert(ROWS >= 1 && ROWS <= 4, "8-bit row fields hold at most 4 rows");
-    static_assert(WARPS <= 16, "16-bit block fields hold at most 16 warps x 128");
+    static_assert(WARPS <= 32, "16-bit block fields hold at most 32 warps x 128 (and one warp scans them)");
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
