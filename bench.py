@@ -52,6 +52,7 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--n", type=int, default=N_LARGE, help="input length (default 2^28; smaller only for profiling)")
+    p.add_argument("--tile", default="", help="block,ipt: fix the tile shape instead of autotuning it")
     return p.parse_args()
 
 
@@ -217,13 +218,18 @@ def run_ours(args):
     ws_t = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
     ws = (ws_t.data_ptr() + 255) // 256 * 256
     ka.check(ka.ka_workspace_init(ws, ws_bytes, st))
-    # the autotuner times every tile shape on this device and keeps the fastest
-    s, tile, tuned_us = ka.ka_autotune(ka.KA_KERNEL_COMPACT, N, None, st)
-    ka.check(s)
+    if args.tile:
+        tile = tuple(int(v) for v in args.tile.split(","))
+        tile_source = "fixed by --tile"
+    else:
+        # the autotuner times every tile shape on this device and keeps the fastest
+        s, tile, tuned_us = ka.ka_autotune(ka.KA_KERNEL_COMPACT, N, None, st)
+        ka.check(s)
+        tile_source = "autotuned (%.1f us at s=50%%)" % tuned_us
 
     def launch(i):
         return ka.ka_compact(x, N, None, ka.KA_PRED_LT, thresholds[i], ka.KA_XFORM_NONE, out, counts[i:i + 1],
-                             ws, ws_bytes, None, st)
+                             ws, ws_bytes, tile, st)
 
     for _ in range(max(args.warmup, 3)):
         for i in range(3):
@@ -279,7 +285,7 @@ def run_ours(args):
                                "t = floor(s 2^32), s = 1%%, 50%%, 99%%; fused single-pass decoupled look-back"
                                % (N.bit_length() - 1),
                    "n": N, "selectivities": list(SELECTIVITIES), "kept": kept, "tile": list(tile),
-                   "tile_source": "autotuned (%.1f us at s=50%%)" % tuned_us,
+                   "tile_source": tile_source,
                    "l2": "inputs (1 GiB) larger than L2; no flush", "parallelism": "replicas x%d" % world},
         "roofline": roofline, "gpu_launches": launches, "clocks": clock_info,
     }

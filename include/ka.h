@@ -343,6 +343,22 @@ ka_status ka_system_monitor(ka_system *sys, ka_monitor_fn fn, void *user);
 ka_status ka_actor_enable_graph(ka_actor *actor, int32_t enable);
 
 /* ------------------------------------------------------------------------ */
+/* Native timing loops for the actor-overhead measurement (Sec. 5.2-5.3: an   */
+/* actor against the same kernels driven directly, task after task).         */
+/* ------------------------------------------------------------------------ */
+/* Sends `msg` to `actor` iters times with at most `inflight` requests
+ * outstanding (1 = each request waits for the previous response), releases
+ * every result, and returns the wall time in *seconds and the last result
+ * length in *last_count. */
+ka_status ka_bench_request_loop(ka_actor *actor, const ka_msg *msg, uint32_t iters, uint32_t inflight,
+                                double *seconds, uint64_t *last_count);
+/* The same stage chain launched directly (no actor layer) on `stream`,
+ * iters times, each followed by a read-back of the result length and a
+ * synchronisation. Buffers are allocated once; three untimed warm-up runs. */
+ka_status ka_bench_direct_chain(const ka_stage_desc *stages, uint32_t n_stages, const uint32_t *d_in, uint64_t n,
+                                uint32_t iters, void *stream, double *seconds, uint64_t *last_count);
+
+/* ------------------------------------------------------------------------ */
 /* Request loop with continuous batching (serving).                          */
 /* ------------------------------------------------------------------------ */
 typedef struct ka_serve_stage {

@@ -158,6 +158,11 @@ _SIGS = {
     "ka_debug_kill_dispatcher": (ctypes.c_int32, [c_vp]),
     "ka_system_monitor": (ctypes.c_int32, [c_vp, MONITOR_FN, c_vp]),
     "ka_actor_enable_graph": (ctypes.c_int32, [c_vp, ctypes.c_int32]),
+    "ka_bench_request_loop": (ctypes.c_int32, [c_vp, ctypes.POINTER(ka_msg), ctypes.c_uint32, ctypes.c_uint32,
+                                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
+    "ka_bench_direct_chain": (ctypes.c_int32, [ctypes.POINTER(ka_stage_desc), ctypes.c_uint32, c_vp, ctypes.c_uint64,
+                                               ctypes.c_uint32, c_vp, ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_uint64)]),
     "ka_serve_run": (ctypes.c_int32, [c_vp, ctypes.POINTER(ka_serve_request), ctypes.c_uint32,
                                       ctypes.POINTER(ka_serve_options), ctypes.POINTER(ka_serve_result),
                                       ctypes.POINTER(ka_serve_stats)]),
@@ -437,3 +442,26 @@ def ka_actor_enable_graph(actor_h, enable: int = 1) -> int:
 
 def ka_serve_run(sys_h, reqs, n_reqs: int, opt, results, stats) -> int:
     return lib.ka_serve_run(sys_h, reqs, n_reqs, ctypes.byref(opt), results, ctypes.byref(stats))
+
+
+def ka_bench_request_loop(actor_h, msg: ka_msg, iters: int, inflight: int = 1):
+    sec, last = ctypes.c_double(0), ctypes.c_uint64(0)
+    s = lib.ka_bench_request_loop(actor_h, ctypes.byref(msg), iters, inflight, ctypes.byref(sec), ctypes.byref(last))
+    return s, sec.value, last.value
+
+
+def stage_descs(specs):
+    """[(kind, pred, param, xform), ...] -> ka_stage_desc array."""
+    arr = (ka_stage_desc * len(specs))()
+    for i, sp in enumerate(specs):
+        kind, pred, param, xform = (tuple(sp) + (0, 0, 0))[:4]
+        arr[i] = ka_stage_desc(kind, pred, param, xform, ka_tile(0, 0))
+    return arr
+
+
+def ka_bench_direct_chain(specs, d_in, n: int, iters: int, stream=None):
+    arr = stage_descs(specs)
+    sec, last = ctypes.c_double(0), ctypes.c_uint64(0)
+    s = lib.ka_bench_direct_chain(arr, len(specs), ptr(d_in), n, iters, stream_ptr(stream), ctypes.byref(sec),
+                                  ctypes.byref(last))
+    return s, sec.value, last.value

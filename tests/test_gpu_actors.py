@@ -171,8 +171,9 @@ def test_fuse_fills_literals_composite(ka, system, fused):
         rest = [spawn(ka, system, ka.KA_STAGE_PREDICATE, ka.KA_PRED_NE, 0), spawn(ka, system, ka.KA_STAGE_EXSCAN),
                 spawn(ka, system, ka.KA_STAGE_SCATTER)]
     pipe = compose(ka, *reversed([prep] + rest))
-    s, ra = ka.ka_ref_wrap(system, to_dev(a), k, k)
-    s, rb = ka.ka_ref_wrap(system, to_dev(b), k, k)
+    d_a, d_b = to_dev(a), to_dev(b)  # borrowed by the refs: keep alive until received
+    s, ra = ka.ka_ref_wrap(system, d_a, k, k)
+    s, rb = ka.ka_ref_wrap(system, d_b, k, k)
     torch.cuda.synchronize()
     out = np.zeros(2 * k, dtype=np.uint32)
     s, req = ka.ka_request(pipe, ka.make_msg([ra, rb], h_out=out))
@@ -195,8 +196,9 @@ def test_compose_type_mismatch(ka, system):
     s, _ = ka.ka_compose(comp, pred)
     assert s == ka.KA_E_TYPE
     # message arity checked at the first stage
-    s, r1 = ka.ka_ref_wrap(system, empty(16), 16, 16)
-    s, r2 = ka.ka_ref_wrap(system, empty(16), 16, 16)
+    d1, d2 = empty(16), empty(16)
+    s, r1 = ka.ka_ref_wrap(system, d1, 16, 16)
+    s, r2 = ka.ka_ref_wrap(system, d2, 16, 16)
     s, req = ka.ka_request(comp, ka.make_msg([r1, r2]))
     assert s == 0
     s, msg = ka.ka_receive(req)
@@ -226,7 +228,8 @@ def test_refs_not_serializable(ka, system):
 def test_pool_returns_to_zero_after_many_requests(ka, system):
     comp = spawn(ka, system, ka.KA_STAGE_COMPACT, ka.KA_PRED_AND_MASK_EQ0, 1)
     x = ki.uniform_u32(8, 50000)
-    s, rx = ka.ka_ref_wrap(system, to_dev(x), x.size, x.size)
+    d_x = to_dev(x)
+    s, rx = ka.ka_ref_wrap(system, d_x, x.size, x.size)
     torch.cuda.synchronize()
     y, k = oracle.compact(x, "and_mask_eq0", 1)
     reqs = []
@@ -248,7 +251,8 @@ def test_budget_rejects_oversized_request(ka):
     assert s == 0
     comp = spawn(ka, sys_h, ka.KA_STAGE_COMPACT, ka.KA_PRED_ALL, 0)
     x = ki.uniform_u32(1, 1 << 20)  # 4 MiB output > 1 MiB budget
-    s, rx = ka.ka_ref_wrap(sys_h, to_dev(x), x.size, x.size)
+    d_x = to_dev(x)
+    s, rx = ka.ka_ref_wrap(sys_h, d_x, x.size, x.size)
     torch.cuda.synchronize()
     s, q = ka.ka_request(comp, ka.make_msg([rx]))
     assert s == 0
