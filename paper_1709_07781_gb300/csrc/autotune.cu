@@ -33,7 +33,7 @@ const ka_tile kShapes[] = {
 };
 
 ka_tile default_tile(int32_t kernel, uint64_t n) {
-    (void)kernel;
+    if (kernel == KA_KERNEL_COMPACT && n >= (1ull << 22)) return ka_tile{512, 16};  // TMA kernel
     if (n >= (1ull << 24)) return ka_tile{256, 16};
     if (n >= (1ull << 21)) return ka_tile{256, 8};
     return ka_tile{256, 4};

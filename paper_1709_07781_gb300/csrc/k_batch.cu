@@ -45,8 +45,8 @@ static BatchLayout batch_layout(void *ws, uint64_t ws_bytes, uint32_t max_items)
     p += round256(uint64_t(max_items) * 32);
     L.status = reinterpret_cast<uint64_t *>(p);
     const uint64_t fixed = batch_fixed_bytes(max_items);
-    const uint64_t words = ws_bytes > fixed ? (ws_bytes - fixed) / 8 : 0;
-    L.status_cap = words > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(words);
+    const uint64_t entries = ws_bytes > fixed ? (ws_bytes - fixed) / kStatusEntryBytes : 0;
+    L.status_cap = entries > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(entries);
     return L;
 }
 
@@ -282,9 +282,7 @@ ka_status ka_batch_workspace_size(uint32_t max_items, uint64_t total_capacity, c
         te = tile->block * tile->ipt;
     }
     const uint64_t tiles = tiles_for(total_capacity, te) + max_items + 1;
-    const uint64_t gen_tiles = tiles_for(total_capacity, kGenTile) + max_items + 1;
-    (void)gen_tiles;
-    *bytes = batch_fixed_bytes(max_items) + round256(tiles * 8);
+    *bytes = batch_fixed_bytes(max_items) + round256(tiles * kStatusEntryBytes);
     return KA_OK;
 }
 
@@ -293,7 +291,7 @@ ka_status ka_compact_batch(const ka_batch_item *d_items, uint32_t n_items, uint3
     if (n_items > max_items || max_items == 0) return KA_E_ARG;
     if (n_items && !d_items) return KA_E_ARG;
     if (!d_ws || (reinterpret_cast<uintptr_t>(d_ws) & 255u) != 0) return KA_E_ARG;
-    if (ws_bytes < batch_fixed_bytes(max_items) + 256) return KA_E_WORKSPACE;
+    if (ws_bytes < batch_fixed_bytes(max_items) + kStatusEntryBytes) return KA_E_WORKSPACE;
     if (n_items == 0) return KA_OK;
     const ka_tile t = resolve_tile(KA_KERNEL_BATCH, 1ull << 17, tile);
     if (!tile_supported(t.block, t.ipt)) return KA_E_ARG;

@@ -97,6 +97,7 @@ ka_status launch_compact(const CompactLaunch &L, cudaStream_t stream) {
     const uint64_t tiles = tiles_for(L.n, t.block * t.ipt);
     const ka_status ws_ok = check_workspace(L.ws, L.ws_bytes, tiles);
     if (ws_ok != KA_OK) return ws_ok;
+    if (compact_tma_eligible(L)) return launch_compact_tma(L, stream);
     CompactArgs a;
     a.in = L.in;
     a.out = L.out;
@@ -105,8 +106,7 @@ ka_status launch_compact(const CompactLaunch &L, cudaStream_t stream) {
     a.ws = static_cast<WsHeader *>(L.ws);
     a.status = reinterpret_cast<uint64_t *>(static_cast<char *>(L.ws) + kWsHeaderBytes);
     a.n = uint32_t(L.n);
-    const uint64_t cap_words = (L.ws_bytes - kWsHeaderBytes) / 8;
-    a.status_cap = cap_words > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(cap_words);
+    a.status_cap = status_capacity(L.ws_bytes);
     a.mul = L.mul;
     a.vec_ok = (reinterpret_cast<uintptr_t>(L.in) & 15u) == 0 ? 1u : 0u;
     a.pred = L.pred;

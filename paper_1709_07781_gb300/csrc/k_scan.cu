@@ -179,8 +179,7 @@ ka_status launch_exclusive_scan(const uint32_t *in, uint64_t n, const uint32_t *
     a.ws = static_cast<WsHeader *>(ws);
     a.status = reinterpret_cast<uint64_t *>(static_cast<char *>(ws) + kWsHeaderBytes);
     a.n = uint32_t(n);
-    const uint64_t cap_words = (ws_bytes - kWsHeaderBytes) / 8;
-    a.status_cap = cap_words > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(cap_words);
+    a.status_cap = status_capacity(ws_bytes);
     a.vec_ok = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) == 0 ? 1u : 0u;
     switch (shape_key(t.block, t.ipt)) {
 #define KA_CASE(B, I) \

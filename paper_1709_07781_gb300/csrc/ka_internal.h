@@ -33,11 +33,18 @@ bool tile_supported(uint32_t block, uint32_t ipt);
 // Shape to use for `kernel` at size n: explicit shape, else autotuned, else default.
 ka_tile resolve_tile(int32_t kernel, uint64_t n, const ka_tile *requested);
 
-// Workspace layout for single-pass kernels.
+// Workspace layout for single-pass kernels: the 256-byte header, then status
+// entries of kStatusStride words. Room for two entries per tile: one per tile
+// plus, for the round-robin kernel, one per iteration (never more than tiles).
 constexpr uint64_t kWsHeaderBytes = 256;
+constexpr uint64_t kStatusEntryBytes = 8 * kStatusStride;
 inline uint64_t tiles_for(uint64_t n, uint32_t tile_elems) { return (n + tile_elems - 1) / tile_elems; }
 inline uint64_t workspace_bytes_for_tiles(uint64_t tiles) {
-    return kWsHeaderBytes + ((tiles * 8 + 255) / 256) * 256;
+    return kWsHeaderBytes + ((2 * tiles * kStatusEntryBytes + 255) / 256) * 256;
+}
+inline uint32_t status_capacity(uint64_t ws_bytes) {
+    const uint64_t e = ws_bytes > kWsHeaderBytes ? (ws_bytes - kWsHeaderBytes) / kStatusEntryBytes : 0;
+    return e > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(e);
 }
 
 // Launchers shared by the C ABI and the actor runtime. All asynchronous.
@@ -54,6 +61,10 @@ struct CompactLaunch {
     ka_tile tile;
 };
 ka_status launch_compact(const CompactLaunch &L, cudaStream_t stream);
+// The warp-specialised TMA kernel (16-byte-aligned input, tile ipt 16 with
+// 256 or 512 threads); launch_compact routes to it when eligible.
+bool compact_tma_eligible(const CompactLaunch &L);
+ka_status launch_compact_tma(const CompactLaunch &L, cudaStream_t stream);
 
 ka_status launch_exclusive_scan(const uint32_t *in, uint64_t n, const uint32_t *n_ptr, uint32_t *out,
                                 uint32_t *total, void *ws, uint64_t ws_bytes, ka_tile tile,

@@ -1,0 +1,110 @@
+"""The warp-specialised TMA compaction (16-byte-aligned input, tile shapes
+(256, 16) and (512, 16)) against the oracle, bit for bit: ragged tails, live
+lengths from a device word, in place, hash transform, empty input, repeated
+launches on one workspace, and the full N = 2^28 workload at 1 %, 50 %, 99 %."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import ka_inputs as ki  # noqa: E402
+import oracle  # noqa: E402
+from gpu_util import SENTINEL, Workspace, empty, stream, to_dev, to_host, word  # noqa: E402
+
+TMA_SHAPES = [(512, 16), (256, 16)]
+
+
+@pytest.fixture(scope="module")
+def ka(cuda_ok):
+    import paper_1709_07781_gb300 as m
+    return m
+
+
+def compact(ka, d_x, n, pred, param, shape, xform=0, d_n=None, out=None, cap=None, ws=None):
+    cap = n if cap is None else cap
+    out = empty(cap + 16) if out is None else out
+    count = empty(1)
+    ws = ws or Workspace(ka, cap, shape)
+    s = ka.ka_compact(d_x, cap if d_n is not None else n, d_n, ka.PRED[pred], param, xform, out, count, ws.ptr,
+                      ws.nbytes, shape, stream())
+    assert s == 0, ka.ka_strerror(s)
+    torch.cuda.synchronize()
+    assert ws.status(ka) == 0
+    return out, word(count)
+
+
+@pytest.mark.parametrize("shape", TMA_SHAPES)
+@pytest.mark.parametrize("n", [1, 4095, 4096, 8191, 8192, 8193, 3 * 8192 + 5, 1 << 20, (1 << 22) + 12345,
+                               (1 << 23) + 1])
+def test_tma_sizes(ka, shape, n):
+    x = ki.uniform_u32(n + 7, n)
+    out, k = compact(ka, to_dev(x), n, "lt", ki.threshold_for(0.37), shape)
+    y, ek = oracle.compact(x, "lt", ki.threshold_for(0.37))
+    assert k == ek
+    assert np.array_equal(to_host(out, k), y)
+    assert np.all(to_host(out)[k:n + 16] == SENTINEL)
+
+
+@pytest.mark.parametrize("shape", TMA_SHAPES)
+@pytest.mark.parametrize("pred,param", [("and_mask_eq0", 3), ("popc_odd", 0), ("mod_ne0", 3), ("ne", 0),
+                                        ("topbits_lt", 8), ("all", 0), ("lt", 0)])
+def test_tma_predicates_and_hash(ka, shape, pred, param):
+    n = (1 << 21) + 333
+    x = ki.uniform_u32(99, n)
+    x[::997] = 0
+    for xform in (0, 1):
+        out, k = compact(ka, to_dev(x), n, pred, param, shape, xform=xform)
+        y, ek = oracle.compact(oracle.map_hash(x) if xform else x, pred, param)
+        assert k == ek and np.array_equal(to_host(out, k), y)
+
+
+@pytest.mark.parametrize("shape", TMA_SHAPES)
+def test_tma_live_length_in_place_and_empty(ka, shape):
+    n = (1 << 22) + 17
+    x = ki.uniform_u32(5, n)
+    # live length from a device word (a previous stage's count)
+    live = 3_000_001
+    d_n = to_dev(np.array([live], dtype=np.uint32))
+    out, k = compact(ka, to_dev(x), n, "popc_odd", 0, shape, d_n=d_n, cap=n)
+    y, ek = oracle.compact(x[:live], "popc_odd", 0)
+    assert k == ek and np.array_equal(to_host(out, k), y)
+    assert np.all(to_host(out)[k:n] == SENTINEL)
+    # in place
+    d = to_dev(x)
+    out, k = compact(ka, d, n, "and_mask_eq0", 1, shape, out=d)
+    y, ek = oracle.compact(x, "and_mask_eq0", 1)
+    assert k == ek and np.array_equal(to_host(d, k), y) and np.array_equal(to_host(d)[k:], x[k:])
+    # empty (host length 0, and device length 0)
+    out, k = compact(ka, empty(16), 0, "all", 0, shape)
+    assert k == 0 and np.all(to_host(out) == SENTINEL)
+    out, k = compact(ka, empty(1 << 16), 1 << 16, "all", 0, shape, d_n=to_dev(np.array([0], dtype=np.uint32)))
+    assert k == 0
+
+
+@pytest.mark.parametrize("shape", TMA_SHAPES)
+def test_tma_workspace_reuse_and_shape_mix(ka, shape):
+    ws = Workspace(ka, 1 << 22, (128, 4))  # sized for the smallest tile: fits every shape
+    for i in range(30):
+        n = [1 << 22, 12345, (1 << 21) + 1, 8192, 77][i % 5]
+        x = ki.uniform_u32(1000 + i, n)
+        sh = shape if i % 3 else (256, 4)  # alternate with the register kernel on one workspace
+        out, k = compact(ka, to_dev(x), n, "lt", ki.threshold_for(0.6), sh, ws=ws)
+        y, ek = oracle.compact(x, "lt", ki.threshold_for(0.6))
+        assert k == ek and np.array_equal(to_host(out, k), y), (i, n, sh)
+
+
+@pytest.mark.parametrize("s", [0.01, 0.5, 0.99])
+def test_full_size_2_28(ka, s):
+    """The benchmark workload itself: N = 2^28 generated on the device (seed 2),
+    keep x < floor(s 2^32), default (autotunable) shape; every output checked."""
+    n = 1 << 28
+    x_dev = torch.empty(n, dtype=torch.int32, device="cuda")
+    assert ka.ka_generate(x_dev, n, 2, stream()) == 0
+    t = ki.threshold_for(s)
+    out, k = compact(ka, x_dev, n, "lt", t, (512, 16))
+    del x_dev
+    x = oracle.generate(2, n)
+    y, ek = oracle.compact(x, "lt", t)
+    assert k == ek
+    assert np.array_equal(to_host(out, k), y)
