@@ -591,9 +591,11 @@ static void dispatcher_main(System *s) {
     auto idle_since = std::chrono::steady_clock::now();
     while (!s->stop.load(std::memory_order_acquire)) {
         if (s->kill_requested.load()) {
-            s->dead.store(true);
+            // mark the actor dead only after its queued work has been failed
+            // and its monitor has been told, so an observer of `dead` sees both
             drain_with(s, KA_E_CLOSED);
             fire_monitor(s, KA_E_CLOSED);
+            s->dead.store(true);
             return;
         }
         QNode *n = s->runq.pop();
