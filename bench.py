@@ -53,6 +53,8 @@ def parse_args():
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--n", type=int, default=N_LARGE, help="input length (default 2^28; smaller only for profiling)")
     p.add_argument("--tile", default="", help="block,ipt: fix the tile shape instead of autotuning it")
+    p.add_argument("--clock-interval-ms", type=int, default=100,
+                   help="nvidia-smi sampling interval during the timed region (0: do not sample)")
     return p.parse_args()
 
 
@@ -107,25 +109,29 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: str, interval_ms: int = 100):
         self.gpu = gpu_index
+        self.interval_ms = interval_ms
         self.proc = None
         self.path = None
 
     def start(self):
+        if self.interval_ms <= 0:
+            return
         try:
             fd, self.path = tempfile.mkstemp(prefix="ka_clocks_", suffix=".csv")
             os.close(fd)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.interval_ms)],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
     def stop(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+            why = "not sampled" if self.interval_ms <= 0 else "nvidia-smi unavailable"
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [why], "samples": 0}
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -240,7 +246,7 @@ def run_ours(args):
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(K)]
     e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(gpu_id_for_smi(torch, local))
+    clocks = ClockSampler(gpu_id_for_smi(torch, local), args.clock_interval_ms)
     D.barrier()
     torch.cuda.synchronize()
     clocks.start()
@@ -258,6 +264,8 @@ def run_ours(args):
     D.barrier()
     total_ms = e_start.elapsed_time(e_end)
     per_sel_ms = [sum(ev[k][2 * i].elapsed_time(ev[k][2 * i + 1]) for k in range(K)) / K for i in range(3)]
+    s_dev, dev_status = ka.ka_workspace_status(ws, st)
+    ka.check(s_dev)
     max_total_s = D.max(total_ms / 1000.0)
     value = aggregate(3.0 * N * K, world, max_total_s)
 
@@ -288,6 +296,7 @@ def run_ours(args):
                    "tile_source": tile_source,
                    "l2": "inputs (1 GiB) larger than L2; no flush", "parallelism": "replicas x%d" % world},
         "roofline": roofline, "gpu_launches": launches, "clocks": clock_info,
+        "device_status": ka.ka_strerror(dev_status), "valid": dev_status == 0,
     }
 
     if not args.no_e2e:
