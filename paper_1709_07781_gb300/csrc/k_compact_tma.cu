@@ -94,6 +94,7 @@ struct TmaArgs {
 template <int CWW, int S, int PF, int MAXG, int MINB>
 __global__ void __launch_bounds__((CWW + 1) * 32, MINB) k_compact_tma(const TmaArgs a) {
     constexpr int NCW = CWW * 32, BLOCK = NCW + 32, ROWS = 4, T = NCW * 16;
+    constexpr int SSTRIDE = T + 32;  // stage: the tile, then 32 scratch slots (16-byte aligned)
     constexpr int K = (MAXG + 31) / 32;
     static_assert(S >= 3, "a counted tile, a tile waiting for its prefix, and one loading");
     extern __shared__ __align__(128) uint32_t stage_mem[];
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__((CWW + 1) * 32, MINB) k_compact_tma(const TmaA
     __shared__ uint32_t s_red[CWW], s_wtot[CWW];
     __shared__ uint64_t s_wexcl[CWW];
     __shared__ uint64_t s_tot;
-    __shared__ uint32_t s_agg[2], s_prefix[2], s_err[2];
+    __shared__ uint32_t s_agg[2], s_prefix[2], s_err[2], s_kept[S];
     __shared__ uint32_t s_n, s_epoch, s_spin, s_pending;
     __shared__ uint32_t s_pend_j[S];  // iteration of the copy outstanding on each stage
 
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__((CWW + 1) * 32, MINB) k_compact_tma(const TmaA
         if (jj >= my_tiles || tile >= full_tiles) return;
         const int s = int(jj % S);
         mbar_expect_tx(&mbar[s], uint32_t(T) * 4u);
-        bulk_g2s(stage_mem + size_t(s) * T, a.in + size_t(tile) * T, uint32_t(T) * 4u, &mbar[s]);
+        bulk_g2s(stage_mem + size_t(s) * SSTRIDE, a.in + size_t(tile) * T, uint32_t(T) * 4u, &mbar[s]);
         s_pending |= 1u << s;
         s_pend_j[s] = jj;
         if (PF > 0) {
@@ -225,12 +226,16 @@ __global__ void __launch_bounds__((CWW + 1) * 32, MINB) k_compact_tma(const TmaA
     }
 
     // -------------------------------------------------------------------- compute warps
+    // Iteration j: count tile j and compact it in place at the front of its
+    // stage (tile-local offsets need no prefix), publish its aggregate; then,
+    // once the look-back warp has the prefix of tile j-1, copy that tile's
+    // compacted run to the output and release its stage.
     const int ct = tid - 32, cw = warp - 1;
     for (uint32_t j = 0; j <= my_tiles; ++j) {
         if (j < my_tiles) {
             const uint32_t tile = b + j * G;
             const int s = int(j % S);
-            uint32_t *buf = stage_mem + size_t(s) * T;
+            uint32_t *buf = stage_mem + size_t(s) * SSTRIDE;
             uint32_t valid = uint32_t(T);
             if (tile < full_tiles) {
                 const uint32_t parity = (j / S) & 1u;
@@ -251,43 +256,11 @@ __global__ void __launch_bounds__((CWW + 1) * 32, MINB) k_compact_tma(const TmaA
                 for (uint32_t e = uint32_t(ct); e < uint32_t(T); e += NCW) buf[e] = e < valid ? src[e] : 0u;
                 bar_sync(1, NCW);
             }
-            uint32_t cnt = 0;
-#pragma unroll
-            for (int r = 0; r < ROWS; ++r) {
-                const uint32_t e0 = uint32_t(r * NCW + ct) * 4;
-                const uint4 q = *reinterpret_cast<const uint4 *>(buf + e0);
-                uint32_t mk = pred_mask4(a.pred, q.x * a.mul, q.y * a.mul, q.z * a.mul, q.w * a.mul);
-                if (valid != uint32_t(T)) {
-                    const uint32_t left = valid > e0 ? valid - e0 : 0u;
-                    mk &= left >= 4 ? 0xFu : ((1u << left) - 1u);
-                }
-                cnt += __popc(mk);
-            }
-            cnt = warp_sum(cnt);
-            if (lane == 0) s_red[cw] = cnt;
-            bar_sync(1, NCW);
-            if (cw == 0) {
-                const uint32_t agg = warp_sum(lane < CWW ? s_red[lane] : 0u);
-                if (lane == 0) {
-                    st_relaxed_u64(status_at(agg_words, tile), pack_status(epoch, kFlagAggregate, agg));
-                    s_agg[j & 1] = agg;
-                }
-            }
-            bar_arrive(2 + int(j & 1), BLOCK);  // hand the count to the look-back warp
-        }
-        if (j >= 1) {
-            const uint32_t jp = j - 1, tile = b + jp * G;
-            bar_sync(4 + int(jp & 1), BLOCK);  // prefix of tile jp ready
-            const int s = int(jp % S);
-            uint32_t *sb = stage_mem + size_t(s) * T;
-            const uint32_t prefix = s_prefix[jp & 1];
-            const bool err = s_err[jp & 1] != 0u;
-            const uint32_t valid = tile < full_tiles ? uint32_t(T) : n - tile * uint32_t(T);
             uint32_t v[ROWS][4], m[ROWS], packed = 0;
 #pragma unroll
             for (int r = 0; r < ROWS; ++r) {
                 const uint32_t e0 = uint32_t(r * NCW + ct) * 4;
-                const uint4 q = *reinterpret_cast<const uint4 *>(sb + e0);
+                const uint4 q = *reinterpret_cast<const uint4 *>(buf + e0);
                 v[r][0] = q.x * a.mul;
                 v[r][1] = q.y * a.mul;
                 v[r][2] = q.z * a.mul;
@@ -303,32 +276,61 @@ __global__ void __launch_bounds__((CWW + 1) * 32, MINB) k_compact_tma(const TmaA
             const uint32_t incl = warp_incl_scan(packed, lane);
             const uint32_t lane_excl = incl - packed;
             if (lane == 31) s_wtot[cw] = incl;
-            bar_sync(1, NCW);  // every compute thread holds its entries; warp totals are in
+            bar_sync(1, NCW);  // every entry of the stage is in registers; warp totals are in
             if (cw == 0) {
                 const uint64_t wt = lane < CWW ? spread8to16(s_wtot[lane]) : 0ull;
                 const uint64_t wi = warp_incl_scan64(wt, lane, CWW);
                 if (lane < CWW) s_wexcl[lane] = wi - wt;
                 const uint64_t total = __shfl_sync(kFull, wi, CWW - 1);  // inclusive total of the last warp
-                if (lane == 0) s_tot = total;
+                const uint32_t agg = uint32_t(total & 0xFFFFu) + uint32_t((total >> 16) & 0xFFFFu) +
+                                     uint32_t((total >> 32) & 0xFFFFu) + uint32_t(total >> 48);
+                if (lane == 0) {
+                    st_relaxed_u64(status_at(agg_words, tile), pack_status(epoch, kFlagAggregate, agg));
+                    s_tot = total;
+                    s_agg[j & 1] = agg;
+                    s_kept[s] = agg;
+                }
             }
             bar_sync(1, NCW);
             const uint64_t tot = s_tot;
             const uint64_t wex = s_wexcl[cw];
             uint32_t rowbase = 0;
+            const uint32_t dummy = uint32_t(T) + uint32_t(lane);  // per-lane scratch slot past the tile
 #pragma unroll
             for (int r = 0; r < ROWS; ++r) {
                 uint32_t off = rowbase + uint32_t((wex >> (16 * r)) & 0xFFFFu) + ((lane_excl >> (8 * r)) & 0xFFu);
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if ((m[r] >> q) & 1u) sb[off++] = v[r][q];
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t keep = (m[r] >> q) & 1u;
+                    buf[keep ? off : dummy] = v[r][q];
+                    off += keep;
+                }
                 rowbase += uint32_t((tot >> (16 * r)) & 0xFFFFu);
             }
-            bar_sync(1, NCW);  // the tile's kept entries are compacted at the front of its stage
-            const uint32_t kept = uint32_t(tot & 0xFFFFu) + uint32_t((tot >> 16) & 0xFFFFu) +
-                                  uint32_t((tot >> 32) & 0xFFFFu) + uint32_t(tot >> 48);
-            if (!err) {
+            bar_arrive(2 + int(j & 1), BLOCK);  // hand the count to the look-back warp
+        }
+        if (j >= 1) {
+            const uint32_t jp = j - 1;
+            bar_sync(4 + int(jp & 1), BLOCK);  // prefix of tile jp ready (and its compaction visible)
+            const int s = int(jp % S);
+            const uint32_t *sb = stage_mem + size_t(s) * SSTRIDE;
+            const uint32_t prefix = s_prefix[jp & 1];
+            const bool err = s_err[jp & 1] != 0u;
+            const uint32_t kept = s_kept[s];
+            if (!err && kept) {
+                // head up to a 16-byte boundary of the output address (the output
+                // itself may start anywhere 4-byte aligned), 16-byte stores, then the tail
                 uint32_t *dst = a.out + prefix;
-                for (uint32_t k = uint32_t(ct); k < kept; k += NCW) dst[k] = sb[k];
+                const uint32_t to_boundary = uint32_t((16u - (reinterpret_cast<uintptr_t>(dst) & 15u)) & 15u) >> 2;
+                const uint32_t head = min(to_boundary, kept);
+                const uint32_t body4 = (kept - head) / 4;
+                const uint32_t tail0 = head + body4 * 4;
+                if (uint32_t(ct) < head) dst[ct] = sb[ct];
+                for (uint32_t i = uint32_t(ct); i < body4; i += NCW) {
+                    const uint32_t k = head + 4 * i;
+                    *reinterpret_cast<uint4 *>(dst + k) = make_uint4(sb[k], sb[k + 1], sb[k + 2], sb[k + 3]);
+                }
+                if (uint32_t(ct) < kept - tail0) dst[tail0 + ct] = sb[tail0 + ct];
             }
             bar_sync(1, NCW);  // stage free
             if (ct == 0) {
@@ -355,7 +357,7 @@ namespace {
 template <int CWW, int S, int PF, int MAXG, int MINB>
 ka_status launch_tma_shape(const TmaArgs &a, uint64_t cap, cudaStream_t stream) {
     constexpr int BLOCK = (CWW + 1) * 32, T = CWW * 32 * 16;
-    const size_t smem = size_t(S) * T * 4;
+    const size_t smem = size_t(S) * (T + 32) * 4;
     auto kern = k_compact_tma<CWW, S, PF, MAXG, MINB>;
     static int grid_cached = 0;
     if (grid_cached == 0) {

@@ -83,6 +83,19 @@ def test_tma_live_length_in_place_and_empty(ka, shape):
 
 
 @pytest.mark.parametrize("shape", TMA_SHAPES)
+@pytest.mark.parametrize("out_off", [1, 2, 3])
+def test_tma_unaligned_output(ka, shape, out_off):
+    """Aligned input (the TMA path) with an output view at every 4-byte offset."""
+    n = (1 << 20) + 77
+    x = ki.uniform_u32(31 + out_off, n)
+    base = empty(n + 32)
+    out, k = compact(ka, to_dev(x), n, "mod_ne0", 5, shape, out=base[out_off:])
+    y, ek = oracle.compact(x, "mod_ne0", 5)
+    assert k == ek and np.array_equal(to_host(base[out_off:], k), y)
+    assert np.all(to_host(base)[:out_off] == SENTINEL) and np.all(to_host(base)[out_off + k:] == SENTINEL)
+
+
+@pytest.mark.parametrize("shape", TMA_SHAPES)
 def test_tma_workspace_reuse_and_shape_mix(ka, shape):
     ws = Workspace(ka, 1 << 22, (128, 4))  # sized for the smallest tile: fits every shape
     for i in range(30):
