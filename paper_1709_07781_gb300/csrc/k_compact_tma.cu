@@ -73,6 +73,7 @@ __device__ __forceinline__ void bar_arrive(int id, int n) {
 }
 
 constexpr uint32_t kMbarSpin = 1u << 22;
+constexpr uint32_t kMaxSkip = 4;  // iterations a look-back may add up instead of waiting for their word
 
 struct TmaArgs {
     const uint32_t *in;
@@ -169,47 +170,114 @@ __global__ void __launch_bounds__((CWW + 1) * 32, MINB) k_compact_tma(const TmaA
             bar_sync(2 + int(j & 1), BLOCK);  // tile j counted; its aggregate is in s_agg
             const uint32_t agg = s_agg[j & 1];
             const uint32_t tile = b + j * G;
+            // prefix = sum of aggregates of tiles (j, 0..b-1)
+            //        + the inclusive word of iteration j-1-d
+            //        + all aggregates of iterations j-d .. j-1,
+            // for the smallest d whose inclusive word is already published
+            // (d = 0 normally); a late word is skipped, not waited for.
             uint32_t sum = 0, polls = 0, sleep_ns = 0;
             bool failed = false;
-            for (;;) {
-                uint64_t raw[K];
+            {
+                // (1) same-iteration predecessors: must be read in full
+                for (;;) {
+                    uint64_t raw[K];
 #pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const uint32_t i = uint32_t(lane) + 32u * k;
-                    raw[k] = i < b ? ld_relaxed_u64(status_at(agg_words, uint64_t(j) * G + i)) : 0ull;
-                }
-                const uint64_t rit = (lane == 0 && j > 0) ? ld_relaxed_u64(status_at(iter_words, j - 1)) : 0ull;
-                bool all = true;
-                sum = 0;
+                    for (int k = 0; k < K; ++k) {
+                        const uint32_t i = uint32_t(lane) + 32u * k;
+                        raw[k] = i < b ? ld_relaxed_u64(status_at(agg_words, uint64_t(j) * G + i)) : 0ull;
+                    }
+                    bool all = true;
+                    sum = 0;
 #pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const uint32_t i = uint32_t(lane) + 32u * k;
-                    if (i < b) {
-                        const uint32_t f = uint32_t(raw[k] >> 34) == want ? uint32_t(raw[k] >> 32) & 3u : kFlagInvalid;
-                        if (f == kFlagAggregate) sum += uint32_t(raw[k]);
-                        else all = false;
+                    for (int k = 0; k < K; ++k) {
+                        const uint32_t i = uint32_t(lane) + 32u * k;
+                        if (i < b) {
+                            const uint32_t f =
+                                uint32_t(raw[k] >> 34) == want ? uint32_t(raw[k] >> 32) & 3u : kFlagInvalid;
+                            if (f == kFlagAggregate) sum += uint32_t(raw[k]);
+                            else all = false;
+                        }
+                    }
+                    if (__all_sync(kFull, all)) break;
+                    if (++polls >= spin) {
+                        failed = true;
+                        if (lane == 0) record_error(a.ws, kDevErrTimeout, tile);
+                        break;
+                    }
+                    if (polls > 2) {
+                        __nanosleep(sleep_ns);
+                        sleep_ns = sleep_ns < 128 ? sleep_ns * 2 + 32 : 128;
                     }
                 }
-                if (lane == 0 && j > 0) {
-                    const uint32_t f = uint32_t(rit >> 34) == want ? uint32_t(rit >> 32) & 3u : kFlagInvalid;
-                    if (f == kFlagInclusive) sum += uint32_t(rit);
-                    else if (f == kFlagError) failed = true;
-                    else all = false;
+                // (2) earlier iterations, newest inclusive word first
+                uint32_t d = 0;
+                uint32_t whole = 0;  // aggregates of whole iterations skipped so far (lane-partial)
+                while (!failed && j > d) {
+                    const uint32_t it = j - 1 - d;  // iteration whose inclusive word is tried
+                    uint64_t rit = 0;
+                    if (lane == 0) rit = ld_relaxed_u64(status_at(iter_words, it));
+                    uint32_t fl = uint32_t(rit >> 34) == want ? uint32_t(rit >> 32) & 3u : kFlagInvalid;
+                    fl = __shfl_sync(kFull, fl, 0);
+                    const uint32_t val = __shfl_sync(kFull, uint32_t(rit), 0);
+                    if (fl == kFlagInclusive) {
+                        if (lane == 0) sum += val;
+                        sum += whole;
+                        whole = 0;
+                        break;
+                    }
+                    if (fl == kFlagError) {
+                        failed = true;
+                        break;
+                    }
+                    if (d + 1 >= kMaxSkip) {  // deep enough: wait for this word
+                        if (++polls >= spin) {
+                            failed = true;
+                            if (lane == 0) record_error(a.ws, kDevErrTimeout, tile);
+                            break;
+                        }
+                        if (polls > 2) {
+                            __nanosleep(sleep_ns);
+                            sleep_ns = sleep_ns < 128 ? sleep_ns * 2 + 32 : 128;
+                        }
+                        continue;
+                    }
+                    // skip iteration `it`: add all of its aggregates instead
+                    for (;;) {
+                        uint64_t raw[K];
+#pragma unroll
+                        for (int k = 0; k < K; ++k) {
+                            const uint32_t i = uint32_t(lane) + 32u * k;
+                            raw[k] = i < G ? ld_relaxed_u64(status_at(agg_words, uint64_t(it) * G + i)) : 0ull;
+                        }
+                        bool all = true;
+                        uint32_t part = 0;
+#pragma unroll
+                        for (int k = 0; k < K; ++k) {
+                            const uint32_t i = uint32_t(lane) + 32u * k;
+                            if (i < G) {
+                                const uint32_t f =
+                                    uint32_t(raw[k] >> 34) == want ? uint32_t(raw[k] >> 32) & 3u : kFlagInvalid;
+                                if (f == kFlagAggregate) part += uint32_t(raw[k]);
+                                else all = false;
+                            }
+                        }
+                        if (__all_sync(kFull, all)) {
+                            whole += part;
+                            break;
+                        }
+                        if (++polls >= spin) {
+                            failed = true;
+                            if (lane == 0) record_error(a.ws, kDevErrTimeout, tile);
+                            break;
+                        }
+                        if (polls > 2) {
+                            __nanosleep(sleep_ns);
+                            sleep_ns = sleep_ns < 128 ? sleep_ns * 2 + 32 : 128;
+                        }
+                    }
+                    ++d;
                 }
-                if (__any_sync(kFull, failed)) {
-                    failed = true;
-                    break;
-                }
-                if (__all_sync(kFull, all)) break;
-                if (++polls >= spin) {
-                    failed = true;
-                    if (lane == 0) record_error(a.ws, kDevErrTimeout, tile);
-                    break;
-                }
-                if (polls > 2) {
-                    __nanosleep(sleep_ns);
-                    sleep_ns = sleep_ns < 128 ? sleep_ns * 2 + 32 : 128;
-                }
+                if (!failed && j <= d) sum += whole;  // reached the first iteration: nothing before it
             }
             const uint32_t prefix = warp_sum(sum);
             if (lane == 0) {
