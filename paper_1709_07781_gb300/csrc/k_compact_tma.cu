@@ -11,21 +11,22 @@
 //     cp.async.bulk (completion on an mbarrier per stage) and, PF iterations
 //     further ahead, cp.async.bulk.prefetch.L2, so HBM reads are in flight
 //     without holding shared memory for them;
-//   * compute warps count the kept entries of tile j and publish that count
-//     (the tile's aggregate) at once, then compact tile j-1 in place in its
-//     stage and write it out at its prefix;
+//   * compute warps count the kept entries of tile j, compact it in place at
+//     the front of its stage and publish the count (the tile's aggregate) at
+//     once; they write a tile out LAG = S - 1 iterations later, when the
+//     look-back warp has long had its prefix, and refill that stage;
 //   * one look-back warp resolves prefixes in tile order. The prefix of tile
 //     (j, b) is the inclusive total of iteration j-1 - a word published by the
 //     last block of that iteration - plus the aggregates of tiles (j, 0..b-1),
-//     all read in one batch of independent loads. The block's own compute warps
-//     need that prefix only one tile later, so the look-back is off their path.
+//     all read in one batch of independent loads (a late iteration word is
+//     replaced by the aggregates of that iteration). The block's own compute
+//     warps need that prefix only LAG tiles later: the look-back is off their path.
 // This is the decoupled look-back of Merrill & Garland (2016) reorganised
 // around a round-robin persistent grid; on GB300 the straightforward form
 // (every block walking back 32 predecessors at a time while its other warps
 // wait) reached about a third of HBM bandwidth, this form reaches 85-100%.
 // The hand-offs between the look-back warp and the compute warps are named
-// barriers (ids 2/3 for counts, 4/5 for prefixes, alternating by tile parity;
-// id 1 synchronises the compute warps).
+// barriers (see kCountBar / kPrefixBar).
 #include "ka_internal.h"
 
 namespace ka {
@@ -74,6 +75,12 @@ __device__ __forceinline__ void bar_arrive(int id, int n) {
 
 constexpr uint32_t kMbarSpin = 1u << 22;
 constexpr uint32_t kMaxSkip = 4;  // iterations a look-back may add up instead of waiting for their word
+// Named barriers: 1 = compute warps only; kCountBar + (t & 3) = tile t counted
+// (compute warps arrive, look-back warp syncs); kPrefixBar + (t & 3) = prefix of
+// tile t resolved (look-back warp arrives, compute warps sync). A period of 4 is
+// at least the lag, so an id is never re-armed before its last use completed.
+constexpr int kCountBar = 2;
+constexpr int kPrefixBar = 6;
 
 struct TmaArgs {
     const uint32_t *in;
@@ -94,16 +101,17 @@ struct TmaArgs {
 // prefetch PF iterations ahead, at most MAXG blocks.
 template <int CWW, int S, int PF, int MAXG, int MINB>
 __global__ void __launch_bounds__((CWW + 1) * 32, MINB) k_compact_tma(const TmaArgs a) {
+    constexpr uint32_t LAG = uint32_t(S) - 1;  // tiles between counting and writing out
     constexpr int NCW = CWW * 32, BLOCK = NCW + 32, ROWS = 4, T = NCW * 16;
     constexpr int SSTRIDE = T + 32;  // stage: the tile, then 32 scratch slots (16-byte aligned)
     constexpr int K = (MAXG + 31) / 32;
-    static_assert(S >= 3, "a counted tile, a tile waiting for its prefix, and one loading");
+    static_assert(S >= 3 && S <= 4, "LAG = S - 1 in [2, 3]: the hand-off barriers and slots repeat every 4 tiles");
     extern __shared__ __align__(128) uint32_t stage_mem[];
     __shared__ __align__(8) uint64_t mbar[S];
     __shared__ uint32_t s_red[CWW], s_wtot[CWW];
     __shared__ uint64_t s_wexcl[CWW];
     __shared__ uint64_t s_tot;
-    __shared__ uint32_t s_agg[2], s_prefix[2], s_err[2], s_kept[S];
+    __shared__ uint32_t s_agg[4], s_prefix[4], s_err[4], s_kept[S];
     __shared__ uint32_t s_n, s_epoch, s_spin, s_pending;
     __shared__ uint32_t s_pend_j[S];  // iteration of the copy outstanding on each stage
 
@@ -167,8 +175,8 @@ __global__ void __launch_bounds__((CWW + 1) * 32, MINB) k_compact_tma(const TmaA
     if (warp == 0) {
         // ---------------------------------------------------------------- look-back warp
         for (uint32_t j = 0; j < my_tiles; ++j) {
-            bar_sync(2 + int(j & 1), BLOCK);  // tile j counted; its aggregate is in s_agg
-            const uint32_t agg = s_agg[j & 1];
+            bar_sync(kCountBar + int(j & 3), BLOCK);  // tile j counted; its aggregate is in s_agg
+            const uint32_t agg = s_agg[j & 3];
             const uint32_t tile = b + j * G;
             // prefix = sum of aggregates of tiles (j, 0..b-1)
             //        + the inclusive word of iteration j-1-d
@@ -285,21 +293,50 @@ __global__ void __launch_bounds__((CWW + 1) * 32, MINB) k_compact_tma(const TmaA
                     st_relaxed_u64(status_at(iter_words, j),
                                    pack_status(epoch, failed ? kFlagError : kFlagInclusive, prefix + agg));
                 if (!failed && tile == live - 1) *a.count = prefix + agg;
-                s_prefix[j & 1] = prefix;
-                s_err[j & 1] = failed ? 1u : 0u;
+                s_prefix[j & 3] = prefix;
+                s_err[j & 3] = failed ? 1u : 0u;
             }
-            bar_arrive(4 + int(j & 1), BLOCK);  // prefix of tile j ready
+            bar_arrive(kPrefixBar + int(j & 3), BLOCK);  // prefix of tile j ready
         }
         return;
     }
 
     // -------------------------------------------------------------------- compute warps
-    // Iteration j: count tile j and compact it in place at the front of its
-    // stage (tile-local offsets need no prefix), publish its aggregate; then,
-    // once the look-back warp has the prefix of tile j-1, copy that tile's
-    // compacted run to the output and release its stage.
+    // Iteration j: first write out tile j-LAG, whose prefix the look-back warp
+    // has had LAG iterations to resolve, and refill its stage with tile
+    // j-LAG+S; then count tile j, compact it in place at the front of its
+    // stage (tile-local offsets need no prefix) and publish its aggregate.
     const int ct = tid - 32, cw = warp - 1;
-    for (uint32_t j = 0; j <= my_tiles; ++j) {
+    for (uint32_t j = 0; j < my_tiles + LAG; ++j) {
+        if (j >= uint32_t(LAG)) {
+            const uint32_t jp = j - LAG;
+            bar_sync(kPrefixBar + int(jp & 3), BLOCK);  // prefix of tile jp ready (and its compaction visible)
+            const int s = int(jp % S);
+            const uint32_t *sb = stage_mem + size_t(s) * SSTRIDE;
+            const uint32_t prefix = s_prefix[jp & 3];
+            const bool err = s_err[jp & 3] != 0u;
+            const uint32_t kept = s_kept[s];
+            if (!err && kept) {
+                // head up to a 16-byte boundary of the output address (the output
+                // itself may start anywhere 4-byte aligned), 16-byte stores, then the tail
+                uint32_t *dst = a.out + prefix;
+                const uint32_t to_boundary = uint32_t((16u - (reinterpret_cast<uintptr_t>(dst) & 15u)) & 15u) >> 2;
+                const uint32_t head = min(to_boundary, kept);
+                const uint32_t body4 = (kept - head) / 4;
+                const uint32_t tail0 = head + body4 * 4;
+                if (uint32_t(ct) < head) dst[ct] = sb[ct];
+                for (uint32_t i = uint32_t(ct); i < body4; i += NCW) {
+                    const uint32_t k = head + 4 * i;
+                    *reinterpret_cast<uint4 *>(dst + k) = make_uint4(sb[k], sb[k + 1], sb[k + 2], sb[k + 3]);
+                }
+                if (uint32_t(ct) < kept - tail0) dst[tail0 + ct] = sb[tail0 + ct];
+            }
+            bar_sync(1, NCW);  // stage free
+            if (ct == 0) {
+                fence_proxy_async();
+                if (!((s_pending >> s) & 1u)) issue(jp + S);  // (a stage whose copy never landed stays idle)
+            }
+        }
         if (j < my_tiles) {
             const uint32_t tile = b + j * G;
             const int s = int(j % S);
@@ -355,7 +392,7 @@ __global__ void __launch_bounds__((CWW + 1) * 32, MINB) k_compact_tma(const TmaA
                 if (lane == 0) {
                     st_relaxed_u64(status_at(agg_words, tile), pack_status(epoch, kFlagAggregate, agg));
                     s_tot = total;
-                    s_agg[j & 1] = agg;
+                    s_agg[j & 3] = agg;
                     s_kept[s] = agg;
                 }
             }
@@ -375,36 +412,7 @@ __global__ void __launch_bounds__((CWW + 1) * 32, MINB) k_compact_tma(const TmaA
                 }
                 rowbase += uint32_t((tot >> (16 * r)) & 0xFFFFu);
             }
-            bar_arrive(2 + int(j & 1), BLOCK);  // hand the count to the look-back warp
-        }
-        if (j >= 1) {
-            const uint32_t jp = j - 1;
-            bar_sync(4 + int(jp & 1), BLOCK);  // prefix of tile jp ready (and its compaction visible)
-            const int s = int(jp % S);
-            const uint32_t *sb = stage_mem + size_t(s) * SSTRIDE;
-            const uint32_t prefix = s_prefix[jp & 1];
-            const bool err = s_err[jp & 1] != 0u;
-            const uint32_t kept = s_kept[s];
-            if (!err && kept) {
-                // head up to a 16-byte boundary of the output address (the output
-                // itself may start anywhere 4-byte aligned), 16-byte stores, then the tail
-                uint32_t *dst = a.out + prefix;
-                const uint32_t to_boundary = uint32_t((16u - (reinterpret_cast<uintptr_t>(dst) & 15u)) & 15u) >> 2;
-                const uint32_t head = min(to_boundary, kept);
-                const uint32_t body4 = (kept - head) / 4;
-                const uint32_t tail0 = head + body4 * 4;
-                if (uint32_t(ct) < head) dst[ct] = sb[ct];
-                for (uint32_t i = uint32_t(ct); i < body4; i += NCW) {
-                    const uint32_t k = head + 4 * i;
-                    *reinterpret_cast<uint4 *>(dst + k) = make_uint4(sb[k], sb[k + 1], sb[k + 2], sb[k + 3]);
-                }
-                if (uint32_t(ct) < kept - tail0) dst[tail0 + ct] = sb[tail0 + ct];
-            }
-            bar_sync(1, NCW);  // stage free
-            if (ct == 0) {
-                fence_proxy_async();
-                if (!((s_pending >> s) & 1u)) issue(jp + S);  // (a stage whose copy never landed stays idle)
-            }
+            bar_arrive(kCountBar + int(j & 3), BLOCK);  // hand the count to the look-back warp
         }
     }
     // Every issued copy has been consumed unless a wait gave up; drain those
