@@ -66,6 +66,7 @@ typedef int32_t ka_status;
 #define KA_E_UNSUPPORTED      -11  /* option not supported                              */
 #define KA_E_INJECTED         -12  /* failure injected on the host by a test hook       */
 #define KA_E_WORKSPACE        -13  /* workspace too small or not initialised            */
+#define KA_E_TOO_LARGE        -14  /* size above ka_compact_static's limit              */
 
 /* Text for a status code (static storage). */
 const char *ka_strerror(ka_status s);
@@ -158,6 +159,33 @@ ka_status ka_scatter(const uint32_t *d_x, const uint32_t *d_flags, const uint32_
 ka_status ka_compact(const uint32_t *d_in, uint64_t n, const uint32_t *d_n, int32_t pred,
                      uint32_t param, uint32_t xform, uint32_t *d_out, uint32_t *d_count,
                      void *d_ws, uint64_t ws_bytes, const ka_tile *tile, void *stream);
+
+/* Compaction for callers that cannot allocate device memory. The paper has
+ * no counterpart: it exists for code that is handed only the buffers it reads
+ * and writes (plug-ins inside another framework's memory management, paths
+ * that must not synchronise, which cudaMalloc and cudaFree may do), and so
+ * cannot supply ka_compact's workspace.
+ *
+ * Same arguments and result as ka_compact without d_ws / ws_bytes: the
+ * workspace is a fixed array of about 2 MiB inside the library, held by every
+ * GPU on which the library's code is loaded until the process exits. The call
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+ * The caller still owns d_in, d_out, d_count and d_n.
+ *
+ * Limit: n (the capacity when d_n is set) <= KA_STATIC_MAX_N = 2^24 entries;
+ * a larger n returns KA_E_TOO_LARGE and launches nothing.
+ * Set-up: the first call on a device (the current device) finds and clears
+ * the array there, on `stream`, and waits for `stream`; make that first call
+ * before any stream capture (during a capture it returns KA_E_UNSUPPORTED).
+ * Every call on a device shares the one array, which keeps what the previous
+ * call left in it; calls whose kernels overlap on the GPU (unordered streams)
+ * race and give undefined results, so order them (one stream, or events).
+ * A device-side look-back timeout is recorded only inside the shared array,
+ * which no entry point reads. */
+#define KA_STATIC_MAX_N (1ull << 24)
+ka_status ka_compact_static(const uint32_t *d_in, uint64_t n, const uint32_t *d_n, int32_t pred,
+                            uint32_t param, uint32_t xform, uint32_t *d_out, uint32_t *d_count,
+                            const ka_tile *tile, void *stream);
 
 /* Interleave of fuseFillsLiterals (Sec. 4.1, Listing 5): d_index[2i] =
  * d_chunk_ids[i], d_index[2i+1] = d_literals[i] for i < live k; d_n_out

@@ -23,6 +23,7 @@ STATUS = {
     0: "KA_OK", -1: "KA_E_ARG", -2: "KA_E_TYPE", -3: "KA_E_OOM", -4: "KA_E_BUDGET", -5: "KA_E_STALE",
     -6: "KA_E_CUDA", -7: "KA_E_DEVICE_TIMEOUT", -8: "KA_E_CLOSED", -9: "KA_E_NOT_SERIALIZABLE",
     -10: "KA_E_TIMEOUT", -11: "KA_E_UNSUPPORTED", -12: "KA_E_INJECTED", -13: "KA_E_WORKSPACE",
+    -14: "KA_E_TOO_LARGE",
 }
 globals().update({v: k for k, v in STATUS.items()})
 
@@ -124,6 +125,8 @@ _SIGS = {
     "ka_scatter": (ctypes.c_int32, [c_vp, c_vp, c_vp, ctypes.c_uint64, c_vp, c_vp, c_vp]),
     "ka_compact": (ctypes.c_int32, [c_vp, ctypes.c_uint64, c_vp, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32,
                                     c_vp, c_vp, c_vp, ctypes.c_uint64, ctypes.POINTER(ka_tile), c_vp]),
+    "ka_compact_static": (ctypes.c_int32, [c_vp, ctypes.c_uint64, c_vp, ctypes.c_int32, ctypes.c_uint32,
+                                           ctypes.c_uint32, c_vp, c_vp, ctypes.POINTER(ka_tile), c_vp]),
     "ka_prepare_index": (ctypes.c_int32, [c_vp, c_vp, ctypes.c_uint64, c_vp, c_vp, c_vp, c_vp]),
     "ka_batch_workspace_size": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(ka_tile),
                                                  ctypes.POINTER(ctypes.c_uint64)]),
@@ -263,6 +266,15 @@ def ka_compact(d_in, n: int, d_n, pred: int, param: int, xform: int, d_out, d_co
                tile=None, stream=None) -> int:
     return lib.ka_compact(ptr(d_in), n, ptr(d_n), pred, param, xform, ptr(d_out), ptr(d_count), ptr(d_ws),
                           ws_bytes, _tile(tile), stream_ptr(stream))
+
+
+KA_STATIC_MAX_N = 1 << 24
+
+
+def ka_compact_static(d_in, n: int, d_n, pred: int, param: int, xform: int, d_out, d_count, tile=None,
+                      stream=None) -> int:
+    return lib.ka_compact_static(ptr(d_in), n, ptr(d_n), pred, param, xform, ptr(d_out), ptr(d_count),
+                                 _tile(tile), stream_ptr(stream))
 
 
 def ka_prepare_index(d_chunk_ids, d_literals, k: int, d_k, d_index, d_n_out=None, stream=None) -> int:

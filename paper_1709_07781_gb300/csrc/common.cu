@@ -89,6 +89,7 @@ const char *ka_strerror(ka_status s) {
     case KA_E_UNSUPPORTED: return "unsupported option";
     case KA_E_INJECTED: return "injected failure (test hook)";
     case KA_E_WORKSPACE: return "workspace too small or not initialised";
+    case KA_E_TOO_LARGE: return "size above the static-scratch limit (KA_STATIC_MAX_N entries)";
     default: return "unknown status";
     }
 }
