@@ -32,8 +32,11 @@ const ka_tile kShapes[] = {
 #undef KA_SHAPE
 };
 
+// Compaction also has the TMA-only shape (768, 16).
+const ka_tile kCompactOnlyShapes[] = {{768, 16}};
+
 ka_tile default_tile(int32_t kernel, uint64_t n) {
-    if (kernel == KA_KERNEL_COMPACT && n >= (1ull << 22)) return ka_tile{512, 16};  // TMA kernel
+    if (kernel == KA_KERNEL_COMPACT && n >= (1ull << 22)) return ka_tile{768, 16};  // TMA kernel
     if (n >= (1ull << 24)) return ka_tile{256, 16};
     if (n >= (1ull << 21)) return ka_tile{256, 8};
     return ka_tile{256, 4};
@@ -87,7 +90,8 @@ bool load_table(const char *path) {
             field(obj, "ipt", &ipt)) {
             field(obj, "us", &us);
             const ka_tile t{uint32_t(block), uint32_t(ipt)};
-            if (tile_supported(t.block, t.ipt)) g_table[{int(kernel), int(bucket)}] = {t, float(us)};
+            if (tile_supported_for(int32_t(kernel), t.block, t.ipt))
+                g_table[{int(kernel), int(bucket)}] = {t, float(us)};
         }
         pos = e + 1;
     }
@@ -171,8 +175,10 @@ ka_status ka_autotune(int32_t kernel, uint64_t n, const char *cache_path, ka_til
     make_pred(KA_PRED_LT, 0x80000000u, &half);
     ka_tile win{0, 0};
     float win_us = 1e30f;
+    std::vector<ka_tile> shapes(std::begin(kShapes), std::end(kShapes));
+    if (kernel == KA_KERNEL_COMPACT) shapes.insert(shapes.end(), std::begin(kCompactOnlyShapes), std::end(kCompactOnlyShapes));
     if (s == KA_OK) {
-        for (const ka_tile &t : kShapes) {
+        for (const ka_tile &t : shapes) {
             auto launch = [&]() -> ka_status {
                 if (kernel == KA_KERNEL_COMPACT) {
                     CompactLaunch L{in, out, nullptr, count, n, half, 1u, ws, ws_bytes, t};

@@ -45,6 +45,10 @@ bool tile_supported(uint32_t block, uint32_t ipt) {
     return false;
 }
 
+bool tile_supported_for(int32_t kernel, uint32_t block, uint32_t ipt) {
+    return tile_supported(block, ipt) || (kernel == KA_KERNEL_COMPACT && tma_shape(block, ipt));
+}
+
 ka_status check_workspace(const void *ws, uint64_t ws_bytes, uint64_t tiles_needed) {
     if (!ws) return KA_E_ARG;
     if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return KA_E_ARG;
@@ -101,7 +105,7 @@ ka_status ka_workspace_size(uint64_t capacity, const ka_tile *tile, uint64_t *by
     if (capacity > 0xFFFFFFFFull) return KA_E_ARG;
     uint32_t te = 512;  // smallest supported tile: enough for every shape
     if (tile && tile->block && tile->ipt) {
-        if (!tile_supported(tile->block, tile->ipt)) return KA_E_ARG;
+        if (!tile_supported(tile->block, tile->ipt) && !tma_shape(tile->block, tile->ipt)) return KA_E_ARG;
         te = tile->block * tile->ipt;
     }
     *bytes = workspace_bytes_for_tiles(tiles_for(capacity, te) + 1);

@@ -93,11 +93,12 @@ ka_status launch_compact(const CompactLaunch &L, cudaStream_t stream) {
     if (!L.count) return KA_E_ARG;
     if (L.n_ptr && L.n_ptr == L.count) return KA_E_ARG;
     const ka_tile t = L.tile;
-    if (!tile_supported(t.block, t.ipt)) return KA_E_ARG;
+    if (!tile_supported_for(KA_KERNEL_COMPACT, t.block, t.ipt)) return KA_E_ARG;
     const uint64_t tiles = tiles_for(L.n, t.block * t.ipt);
     const ka_status ws_ok = check_workspace(L.ws, L.ws_bytes, tiles);
     if (ws_ok != KA_OK) return ws_ok;
     if (compact_tma_eligible(L)) return launch_compact_tma(L, stream);
+    if (!tile_supported(t.block, t.ipt)) return KA_E_ARG;  // a TMA-only shape beyond its size limit
     CompactArgs a;
     a.in = L.in;
     a.out = L.out;

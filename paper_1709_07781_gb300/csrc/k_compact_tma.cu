@@ -1,32 +1,38 @@
-// Fused single-pass compaction for 16-byte-aligned inputs: a persistent,
-// warp-specialised kernel fed by TMA bulk copies.
+// Fused single-pass compaction: a persistent, warp-specialised kernel fed by
+// TMA bulk copies, whose compute warps never wait for one another.
 //
 // Layout of the work. The grid holds exactly the blocks that fit on the GPU at
 // once (cooperative launch), G of them; block b owns tiles b, b + G, b + 2G, ...
-// (iteration j of block b is tile j G + b), so at any moment the G blocks work
-// on one contiguous window of G tiles.
+// (iteration j of block b is tile t = j G + b). A tile is CWW segments of 512
+// entries; compute warp w owns segment w of every tile. Tiles start on
+// 16-byte boundaries: an input that starts 4, 8 or 12 bytes past one is read
+// from that boundary, and the 1-3 entries before its start belong to no tile.
 //
 // Inside a block:
-//   * one thread streams tiles into a ring of S shared-memory stages with
-//     cp.async.bulk (completion on an mbarrier per stage) and, PF iterations
-//     further ahead, cp.async.bulk.prefetch.L2, so HBM reads are in flight
-//     without holding shared memory for them;
-//   * compute warps count the kept entries of tile j, compact it in place at
-//     the front of its stage and publish the count (the tile's aggregate) at
-//     once; they write a tile out LAG = S - 1 iterations later, when the
-//     look-back warp has long had its prefix, and refill that stage;
-//   * one look-back warp resolves prefixes in tile order. The prefix of tile
-//     (j, b) is the inclusive total of iteration j-1 - a word published by the
-//     last block of that iteration - plus the aggregates of tiles (j, 0..b-1),
-//     all read in one batch of independent loads (a late iteration word is
-//     replaced by the aggregates of that iteration). The block's own compute
-//     warps need that prefix only LAG tiles later: the look-back is off their path.
+//   * a producer warp streams tiles into a ring of S shared-memory stages
+//     with cp.async.bulk (completion on the stage's "full" mbarrier), and
+//     refills a stage once every compute warp has released it ("empty");
+//   * each compute warp counts the kept entries of its segment of tile j,
+//     compacts them in place at the front of the segment (a warp-local
+//     operation) and posts its count ("counted" mbarrier of tile j); the
+//     last warp to post publishes the tile aggregate at once (an atomic on a
+//     shared word tells it that it is last). LAG iterations later the warp
+//     copies its compacted segment to the output at the offset the look-back
+//     warp left for it ("prefix" mbarrier) and releases the stage;
+//   * one look-back warp resolves the tiles' exclusive prefixes in order.
+//     The prefix of tile t is anchored on the block's own previous tile,
+//     prefix(t) = prefix(t - G) + agg(t - G) + the aggregates of the G - 1
+//     tiles t - G + 1 .. t - 1, so a tile costs one batch of independent
+//     loads of aggregates, which the other blocks publish as soon as they
+//     have counted, and no block waits for another block's look-back.
 // This is the decoupled look-back of Merrill & Garland (2016) reorganised
-// around a round-robin persistent grid; on GB300 the straightforward form
-// (every block walking back 32 predecessors at a time while its other warps
-// wait) reached about a third of HBM bandwidth, this form reaches 85-100%.
-// The hand-offs between the look-back warp and the compute warps are named
-// barriers (see kCountBar / kPrefixBar).
+// around a round-robin persistent grid. The look-back's loads queue behind
+// the SM's own stream of copies, so its round trip is about a microsecond;
+// the LAG tiles between counting and writing out hide it, and large tiles
+// (one 24-warp block per SM) keep the number of round trips low.
+// One lane per warp arrives on an mbarrier, after __syncwarp: 32 arrivals on
+// one barrier word serialise. Every wait is bounded (a few seconds); on
+// time-out the kernel records a device error and still finishes.
 #include "ka_internal.h"
 
 namespace ka {
@@ -36,6 +42,10 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) { return uint32_t(_
 
 __device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *m) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(m)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *m, uint32_t bytes) {
@@ -53,6 +63,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity) {
     return ok != 0;
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits until the phase of parity `parity` of m has completed. Gives up after
+// kWaitNs of wall time and returns false.
+constexpr uint64_t kWaitNs = 2000000000ull;
+__device__ __forceinline__ bool mbar_wait(uint64_t *m, uint32_t parity) {
+    if (mbar_try_wait(m, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try_wait(m, parity)) return true;
+        if ((i & 15u) == 0u && global_ns() - t0 > kWaitNs) return false;
+    }
+}
+
 // Bulk copy global -> this block's shared memory, completing on mbarrier m.
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *m) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -61,29 +89,12 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  : "memory");
 }
 
-__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
-
-__device__ __forceinline__ void bar_arrive(int id, int n) {
-    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-
-constexpr uint32_t kMbarSpin = 1u << 22;
-constexpr uint32_t kMaxSkip = 4;  // iterations a look-back may add up instead of waiting for their word
-// Named barriers: 1 = compute warps only; kCountBar + (t & 3) = tile t counted
-// (compute warps arrive, look-back warp syncs); kPrefixBar + (t & 3) = prefix of
-// tile t resolved (look-back warp arrives, compute warps sync). A period of 4 is
-// at least the lag, so an id is never re-armed before its last use completed.
-constexpr int kCountBar = 2;
-constexpr int kPrefixBar = 6;
+constexpr int kSeg = 512;         // entries per compute warp and tile (32 lanes x 4 rows x 4)
 
 struct TmaArgs {
-    const uint32_t *in;
+    const uint32_t *in;  // input rounded down to 16 bytes: entry i of the input is in[lead + i]
     uint32_t *out;
     const uint32_t *n_ptr;
     uint32_t *count;
@@ -92,28 +103,66 @@ struct TmaArgs {
     uint32_t n;
     uint32_t status_cap;
     uint32_t mul;
+    uint32_t lead;  // 0..3 entries before the input's first entry
     PredDev pred;
 };
 
+// One warp copies cnt compacted entries from shared memory (16-byte aligned)
+// to dst (4-byte aligned): single entries up to dst's next 16-byte boundary,
+// then 16-byte stores, each assembled from two aligned 16-byte shared loads,
+// then the remaining single entries. cnt <= kSeg.
+__device__ __forceinline__ void warp_copy_out(const uint32_t *src, uint32_t *dst, uint32_t cnt, int lane) {
+    const uint32_t to16 = uint32_t((16u - (reinterpret_cast<uintptr_t>(dst) & 15u)) & 15u) >> 2;
+    const uint32_t head = to16 < cnt ? to16 : cnt;
+    if (uint32_t(lane) < head) dst[lane] = src[lane];
+    const uint32_t body = (cnt - head) >> 2;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst + head);
+    // Output chunk i holds src[head + 4i .. head + 4i + 3]: the tail of source
+    // chunk i and the front of chunk i + 1 (index <= 127 since cnt <= 512).
+    switch (head) {
+    case 0:
+        for (uint32_t i = uint32_t(lane); i < body; i += 32) d4[i] = s4[i];
+        break;
+    case 1:
+        for (uint32_t i = uint32_t(lane); i < body; i += 32) {
+            const uint4 x = s4[i], y = s4[i + 1];
+            d4[i] = make_uint4(x.y, x.z, x.w, y.x);
+        }
+        break;
+    case 2:
+        for (uint32_t i = uint32_t(lane); i < body; i += 32) {
+            const uint4 x = s4[i], y = s4[i + 1];
+            d4[i] = make_uint4(x.z, x.w, y.x, y.y);
+        }
+        break;
+    default:
+        for (uint32_t i = uint32_t(lane); i < body; i += 32) {
+            const uint4 x = s4[i], y = s4[i + 1];
+            d4[i] = make_uint4(x.w, y.x, y.y, y.z);
+        }
+        break;
+    }
+    const uint32_t t0 = head + 4 * body;
+    if (uint32_t(lane) < cnt - t0) dst[t0 + lane] = src[t0 + lane];
+}
+
 }  // namespace
 
-// CWW compute warps (tile = CWW * 32 threads * 16 entries), S stages, L2
-// prefetch PF iterations ahead, at most MAXG blocks.
-template <int CWW, int S, int PF, int MAXG, int MINB>
-__global__ void __launch_bounds__((CWW + 1) * 32, MINB) k_compact_tma(const TmaArgs a) {
-    constexpr uint32_t LAG = uint32_t(S) - 1;  // tiles between counting and writing out
-    constexpr int NCW = CWW * 32, BLOCK = NCW + 32, ROWS = 4, T = NCW * 16;
-    constexpr int SSTRIDE = T + 32;  // stage: the tile, then 32 scratch slots (16-byte aligned)
+// CWW compute warps (tile = CWW * 512 entries), S stages, write-out LAG tiles
+// after counting, at most MAXG blocks, MINB blocks per SM.
+template <int CWW, int S, int LAG, int MAXG, int MINB>
+__global__ void __launch_bounds__((CWW + 2) * 32, MINB) k_compact_tma(const TmaArgs a) {
+    constexpr int T = CWW * kSeg, ROWS = 4;
     constexpr int K = (MAXG + 31) / 32;
-    static_assert(S >= 3 && S <= 4, "LAG = S - 1 in [2, 3]: the hand-off barriers and slots repeat every 4 tiles");
+    static_assert(LAG >= 1 && LAG < S && LAG <= 3, "a stage is written out before its refill; slots repeat every 4");
+    static_assert(CWW <= 32, "the look-back warp holds one segment count per lane");
+    static_assert(CWW * kSeg < 65536, "a tile aggregate fits the 16 low bits of s_pack");
     extern __shared__ __align__(128) uint32_t stage_mem[];
-    __shared__ __align__(8) uint64_t mbar[S];
-    __shared__ uint32_t s_red[CWW], s_wtot[CWW];
-    __shared__ uint64_t s_wexcl[CWW];
-    __shared__ uint64_t s_tot;
-    __shared__ uint32_t s_agg[4], s_prefix[4], s_err[4], s_kept[S];
-    __shared__ uint32_t s_n, s_epoch, s_spin, s_pending;
-    __shared__ uint32_t s_pend_j[S];  // iteration of the copy outstanding on each stage
+    __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], count_bar[4], prefix_bar[4];
+    __shared__ uint32_t s_wcnt[4][CWW], s_woff[4][CWW], s_err[4];
+    __shared__ uint32_t s_pack[4];  // per tile slot: (segments counted << 16) | kept so far
+    __shared__ uint32_t s_n, s_epoch, s_spin;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t G = gridDim.x, b = blockIdx.x;
@@ -131,310 +180,229 @@ __global__ void __launch_bounds__((CWW + 1) * 32, MINB) k_compact_tma(const TmaA
         bool last;
         take_ticket(a.ws, 0u, &ep, &last);  // one ticket per block: the epoch; the last block resets
         s_epoch = ep;
-        s_pending = 0;
-        for (int s = 0; s < S; ++s) mbar_init(&mbar[s], 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], CWW);
+        }
+        for (int k = 0; k < 4; ++k) {
+            s_pack[k] = 0;
+            mbar_init(&count_bar[k], CWW);
+            mbar_init(&prefix_bar[k], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const uint32_t n = s_n, epoch = s_epoch, want = epoch & kEpochMask, spin = s_spin;
+    // Tiles cover the input shifted by `lead` entries, so that every tile
+    // starts on a 16-byte boundary; the lead entries belong to no tile.
+    const uint32_t n_in = s_n, n = n_in + a.lead;
+    const uint32_t epoch = s_epoch, want = epoch & kEpochMask, spin = s_spin;
     const uint32_t live = uint32_t((uint64_t(n) + T - 1) / T);
     const uint32_t full_tiles = n / uint32_t(T);
-    const uint32_t iters = (live + G - 1) / G;
-    if (uint64_t(live) + iters > a.status_cap) {
+    if (uint64_t(live) > a.status_cap) {
         if (tid == 0 && b == 0) record_error(a.ws, kDevErrWorkspace, 0);
         return;
     }
-    if (live == 0) {
+    if (n_in == 0) {
         if (tid == 0 && b == 0) *a.count = 0u;
         return;
     }
     const uint32_t my_tiles = live > b ? (live - b + G - 1) / G : 0u;
-    uint64_t *agg_words = a.status;                   // entry per tile
-    uint64_t *iter_words = a.status + uint64_t(live) * kStatusStride;  // entry per iteration
+    uint64_t *agg_words = a.status;  // entry per tile
 
-    // Issues the load of this block's tile jj into stage jj % S (full tiles
-    // only; the ragged last tile is read by the compute warps themselves).
-    auto issue = [&](uint32_t jj) {
-        const uint32_t tile = b + jj * G;
-        if (jj >= my_tiles || tile >= full_tiles) return;
-        const int s = int(jj % S);
-        mbar_expect_tx(&mbar[s], uint32_t(T) * 4u);
-        bulk_g2s(stage_mem + size_t(s) * SSTRIDE, a.in + size_t(tile) * T, uint32_t(T) * 4u, &mbar[s]);
-        s_pending |= 1u << s;
-        s_pend_j[s] = jj;
-        if (PF > 0) {
-            const uint32_t pj = jj + PF;
-            const uint32_t pt = b + pj * G;
-            if (pj < my_tiles && pt < full_tiles) prefetch_l2(a.in + size_t(pt) * T, uint32_t(T) * 4u);
+    if (warp == CWW + 1) {
+        // ------------------------------------------------------------------ producer warp
+        if (lane != 0) return;
+        uint32_t issued = 0;
+        for (uint32_t jj = 0; jj < my_tiles; ++jj) {
+            const uint32_t tile = b + jj * G;
+            if (tile >= full_tiles) break;  // the ragged last tile is read by the compute warps
+            const int s = int(jj % S);
+            if (jj >= uint32_t(S) && !mbar_wait(&empty_bar[s], ((jj / S) - 1u) & 1u)) {
+                record_error(a.ws, kDevErrTimeout, tile);
+                break;
+            }
+            fence_proxy_async();  // the compute warps' writes to this stage precede the copy into it
+            mbar_expect_tx(&full_bar[s], uint32_t(T) * 4u);
+            bulk_g2s(stage_mem + size_t(s) * T, a.in + size_t(tile) * T, uint32_t(T) * 4u, &full_bar[s]);
+            issued = jj + 1;
         }
-    };
-    if (tid == 0)
-        for (uint32_t jj = 0; jj < uint32_t(S); ++jj) issue(jj);
-    __syncthreads();
+        // Every copy has been consumed unless a wait gave up; wait (bounded)
+        // for the last one on each stage so none lands after the block exits.
+        for (uint32_t jj = issued > uint32_t(S) ? issued - S : 0u; jj < issued; ++jj)
+            mbar_wait(&full_bar[jj % S], (jj / S) & 1u);
+        return;
+    }
 
-    if (warp == 0) {
+    if (warp == CWW) {
         // ---------------------------------------------------------------- look-back warp
+        // The prefix of tile t = j G + b is anchored on this block's own
+        // previous tile: prefix(t) = prefix(t - G) + agg(t - G) + the
+        // aggregates of the G - 1 tiles in between, t - G + 1 .. t - 1 (for
+        // j = 0: the aggregates of tiles 0 .. t - 1). The anchor is a
+        // register, so a tile costs one batch of independent loads of
+        // aggregates, which other blocks publish as soon as they have counted,
+        // and no block waits for another block's look-back.
+        uint32_t incl_prev = 0;  // inclusive prefix of this block's previous tile
+        bool broken = false;     // an earlier look-back of this block gave up
         for (uint32_t j = 0; j < my_tiles; ++j) {
-            bar_sync(kCountBar + int(j & 3), BLOCK);  // tile j counted; its aggregate is in s_agg
-            const uint32_t agg = s_agg[j & 3];
-            const uint32_t tile = b + j * G;
-            // prefix = sum of aggregates of tiles (j, 0..b-1)
-            //        + the inclusive word of iteration j-1-d
-            //        + all aggregates of iterations j-d .. j-1,
-            // for the smallest d whose inclusive word is already published
-            // (d = 0 normally); a late word is skipped, not waited for.
+            const uint32_t k = j & 3u, tile = b + j * G;
+            bool failed = !mbar_wait(&count_bar[k], (j >> 2) & 1u);  // every segment of tile j counted
+            if (failed && lane == 0) record_error(a.ws, kDevErrTimeout, tile);
+            const uint32_t wc = lane < CWW ? s_wcnt[k][lane] : 0u;
+            const uint32_t wincl = warp_incl_scan(wc, lane);
+            const uint32_t agg = __shfl_sync(kFull, wincl, 31);  // (published by the last warp to count)
+            const uint32_t lo = j == 0 ? 0u : tile - G + 1u;     // first tile of the window
+            const uint32_t wn = tile - lo;                       // window length, < G
             uint32_t sum = 0, polls = 0, sleep_ns = 0;
-            bool failed = false;
-            {
-                // (1) same-iteration predecessors: must be read in full
-                for (;;) {
-                    uint64_t raw[K];
+            failed = failed || broken;
+            while (!failed) {
+                uint64_t raw[K];
 #pragma unroll
-                    for (int k = 0; k < K; ++k) {
-                        const uint32_t i = uint32_t(lane) + 32u * k;
-                        raw[k] = i < b ? ld_relaxed_u64(status_at(agg_words, uint64_t(j) * G + i)) : 0ull;
-                    }
-                    bool all = true;
-                    sum = 0;
+                for (int kk = 0; kk < K; ++kk) {
+                    const uint32_t i = uint32_t(lane) + 32u * kk;
+                    raw[kk] = i < wn ? ld_relaxed_u64(status_at(agg_words, uint64_t(lo) + i)) : 0ull;
+                }
+                bool all = true;
+                sum = 0;
 #pragma unroll
-                    for (int k = 0; k < K; ++k) {
-                        const uint32_t i = uint32_t(lane) + 32u * k;
-                        if (i < b) {
-                            const uint32_t f =
-                                uint32_t(raw[k] >> 34) == want ? uint32_t(raw[k] >> 32) & 3u : kFlagInvalid;
-                            if (f == kFlagAggregate) sum += uint32_t(raw[k]);
-                            else all = false;
-                        }
-                    }
-                    if (__all_sync(kFull, all)) break;
-                    if (++polls >= spin) {
-                        failed = true;
-                        if (lane == 0) record_error(a.ws, kDevErrTimeout, tile);
-                        break;
-                    }
-                    if (polls > 2) {
-                        __nanosleep(sleep_ns);
-                        sleep_ns = sleep_ns < 128 ? sleep_ns * 2 + 32 : 128;
+                for (int kk = 0; kk < K; ++kk) {
+                    const uint32_t i = uint32_t(lane) + 32u * kk;
+                    if (i < wn) {
+                        const uint32_t f =
+                            uint32_t(raw[kk] >> 34) == want ? uint32_t(raw[kk] >> 32) & 3u : kFlagInvalid;
+                        if (f == kFlagAggregate) sum += uint32_t(raw[kk]);
+                        else all = false;
                     }
                 }
-                // (2) earlier iterations, newest inclusive word first
-                uint32_t d = 0;
-                uint32_t whole = 0;  // aggregates of whole iterations skipped so far (lane-partial)
-                while (!failed && j > d) {
-                    const uint32_t it = j - 1 - d;  // iteration whose inclusive word is tried
-                    uint64_t rit = 0;
-                    if (lane == 0) rit = ld_relaxed_u64(status_at(iter_words, it));
-                    uint32_t fl = uint32_t(rit >> 34) == want ? uint32_t(rit >> 32) & 3u : kFlagInvalid;
-                    fl = __shfl_sync(kFull, fl, 0);
-                    const uint32_t val = __shfl_sync(kFull, uint32_t(rit), 0);
-                    if (fl == kFlagInclusive) {
-                        if (lane == 0) sum += val;
-                        sum += whole;
-                        whole = 0;
-                        break;
-                    }
-                    if (fl == kFlagError) {
-                        failed = true;
-                        break;
-                    }
-                    if (d + 1 >= kMaxSkip) {  // deep enough: wait for this word
-                        if (++polls >= spin) {
-                            failed = true;
-                            if (lane == 0) record_error(a.ws, kDevErrTimeout, tile);
-                            break;
-                        }
-                        if (polls > 2) {
-                            __nanosleep(sleep_ns);
-                            sleep_ns = sleep_ns < 128 ? sleep_ns * 2 + 32 : 128;
-                        }
-                        continue;
-                    }
-                    // skip iteration `it`: add all of its aggregates instead
-                    for (;;) {
-                        uint64_t raw[K];
-#pragma unroll
-                        for (int k = 0; k < K; ++k) {
-                            const uint32_t i = uint32_t(lane) + 32u * k;
-                            raw[k] = i < G ? ld_relaxed_u64(status_at(agg_words, uint64_t(it) * G + i)) : 0ull;
-                        }
-                        bool all = true;
-                        uint32_t part = 0;
-#pragma unroll
-                        for (int k = 0; k < K; ++k) {
-                            const uint32_t i = uint32_t(lane) + 32u * k;
-                            if (i < G) {
-                                const uint32_t f =
-                                    uint32_t(raw[k] >> 34) == want ? uint32_t(raw[k] >> 32) & 3u : kFlagInvalid;
-                                if (f == kFlagAggregate) part += uint32_t(raw[k]);
-                                else all = false;
-                            }
-                        }
-                        if (__all_sync(kFull, all)) {
-                            whole += part;
-                            break;
-                        }
-                        if (++polls >= spin) {
-                            failed = true;
-                            if (lane == 0) record_error(a.ws, kDevErrTimeout, tile);
-                            break;
-                        }
-                        if (polls > 2) {
-                            __nanosleep(sleep_ns);
-                            sleep_ns = sleep_ns < 128 ? sleep_ns * 2 + 32 : 128;
-                        }
-                    }
-                    ++d;
+                if (__all_sync(kFull, all)) break;
+                if (++polls >= spin) {
+                    failed = true;
+                    if (lane == 0) record_error(a.ws, kDevErrTimeout, tile);
+                    break;
                 }
-                if (!failed && j <= d) sum += whole;  // reached the first iteration: nothing before it
+                if (polls > 2) {
+                    __nanosleep(sleep_ns);
+                    sleep_ns = sleep_ns < 128 ? sleep_ns * 2 + 32 : 128;
+                }
             }
-            const uint32_t prefix = warp_sum(sum);
+            const uint32_t prefix = incl_prev + warp_sum(sum);
+            broken = failed;
+            incl_prev = prefix + agg;
+            if (lane < CWW) s_woff[k][lane] = prefix + wincl - wc;
             if (lane == 0) {
-                if (b == G - 1 || tile == live - 1)
-                    st_relaxed_u64(status_at(iter_words, j),
-                                   pack_status(epoch, failed ? kFlagError : kFlagInclusive, prefix + agg));
                 if (!failed && tile == live - 1) *a.count = prefix + agg;
-                s_prefix[j & 3] = prefix;
-                s_err[j & 3] = failed ? 1u : 0u;
+                s_err[k] = failed ? 1u : 0u;
             }
-            bar_arrive(kPrefixBar + int(j & 3), BLOCK);  // prefix of tile j ready
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&prefix_bar[k]);  // offsets of tile j ready
         }
         return;
     }
 
-    // -------------------------------------------------------------------- compute warps
-    // Iteration j: first write out tile j-LAG, whose prefix the look-back warp
-    // has had LAG iterations to resolve, and refill its stage with tile
-    // j-LAG+S; then count tile j, compact it in place at the front of its
-    // stage (tile-local offsets need no prefix) and publish its aggregate.
-    const int ct = tid - 32, cw = warp - 1;
-    for (uint32_t j = 0; j < my_tiles + LAG; ++j) {
+    // ---------------------------------------------------------------- compute warps
+    // Iteration j: write out this warp's segment of tile j-LAG, whose offsets
+    // the look-back warp has had LAG iterations to resolve, and release its
+    // stage; then count the segment of tile j, compact it in place and post
+    // the count.
+    const int w = warp;
+    const uint32_t mul = a.mul;
+    uint32_t *const seg_base = stage_mem + w * kSeg;
+    for (uint32_t j = 0; j < my_tiles + uint32_t(LAG); ++j) {
         if (j >= uint32_t(LAG)) {
-            const uint32_t jp = j - LAG;
-            bar_sync(kPrefixBar + int(jp & 3), BLOCK);  // prefix of tile jp ready (and its compaction visible)
+            const uint32_t jp = j - uint32_t(LAG), k = jp & 3u;
             const int s = int(jp % S);
-            const uint32_t *sb = stage_mem + size_t(s) * SSTRIDE;
-            const uint32_t prefix = s_prefix[jp & 3];
-            const bool err = s_err[jp & 3] != 0u;
-            const uint32_t kept = s_kept[s];
-            if (!err && kept) {
-                // head up to a 16-byte boundary of the output address (the output
-                // itself may start anywhere 4-byte aligned), 16-byte stores, then the tail
-                uint32_t *dst = a.out + prefix;
-                const uint32_t to_boundary = uint32_t((16u - (reinterpret_cast<uintptr_t>(dst) & 15u)) & 15u) >> 2;
-                const uint32_t head = min(to_boundary, kept);
-                const uint32_t body4 = (kept - head) / 4;
-                const uint32_t tail0 = head + body4 * 4;
-                if (uint32_t(ct) < head) dst[ct] = sb[ct];
-                for (uint32_t i = uint32_t(ct); i < body4; i += NCW) {
-                    const uint32_t k = head + 4 * i;
-                    *reinterpret_cast<uint4 *>(dst + k) = make_uint4(sb[k], sb[k + 1], sb[k + 2], sb[k + 3]);
-                }
-                if (uint32_t(ct) < kept - tail0) dst[tail0 + ct] = sb[tail0 + ct];
-            }
-            bar_sync(1, NCW);  // stage free
-            if (ct == 0) {
-                fence_proxy_async();
-                if (!((s_pending >> s) & 1u)) issue(jp + S);  // (a stage whose copy never landed stays idle)
-            }
+            const bool ok = mbar_wait(&prefix_bar[k], (jp >> 2) & 1u);
+            if (!ok && lane == 0) record_error(a.ws, kDevErrTimeout, b + jp * G);
+            const uint32_t cnt = s_wcnt[k][w];
+            const uint32_t off = s_woff[k][w];
+            __syncwarp();
+            if (ok && s_err[k] == 0u && cnt != 0u) warp_copy_out(seg_base + size_t(s) * T, a.out + off, cnt, lane);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty_bar[s]);  // this warp is done with the stage
         }
         if (j < my_tiles) {
-            const uint32_t tile = b + j * G;
+            const uint32_t tile = b + j * G, k = j & 3u;
             const int s = int(j % S);
-            uint32_t *buf = stage_mem + size_t(s) * SSTRIDE;
-            uint32_t valid = uint32_t(T);
+            uint32_t *seg = seg_base + size_t(s) * T;
+            // entries [vlo, vhi) of this segment are input entries
+            const uint32_t base = tile * uint32_t(T) + uint32_t(w) * kSeg;
+            const uint32_t vlo = base < a.lead ? a.lead - base : 0u;
+            const uint32_t vhi = n > base ? min(n - base, uint32_t(kSeg)) : 0u;
             if (tile < full_tiles) {
-                const uint32_t parity = (j / S) & 1u;
-                uint32_t polls = 0;
-                bool ok = true;
-                while (!mbar_try_wait(&mbar[s], parity)) {
-                    if (++polls > kMbarSpin) {
-                        record_error(a.ws, kDevErrTimeout, tile);
-                        ok = false;
-                        break;
-                    }
-                }
-                if (ok && ct == 0) s_pending &= ~(1u << s);  // the copy has landed
+                if (!mbar_wait(&full_bar[s], (j / S) & 1u) && lane == 0) record_error(a.ws, kDevErrTimeout, tile);
             } else {
-                // ragged last tile: plain loads into the stage, zeros past the end
-                valid = n - tile * uint32_t(T);
-                const uint32_t *src = a.in + size_t(tile) * T;
-                for (uint32_t e = uint32_t(ct); e < uint32_t(T); e += NCW) buf[e] = e < valid ? src[e] : 0u;
-                bar_sync(1, NCW);
+                // ragged last tile: plain loads of this segment, zeros outside the input
+                const uint32_t *src = a.in + base;
+                for (uint32_t e = uint32_t(lane); e < uint32_t(kSeg); e += 32)
+                    seg[e] = e >= vlo && e < vhi ? src[e] : 0u;
+                __syncwarp();
             }
             uint32_t v[ROWS][4], m[ROWS], packed = 0;
 #pragma unroll
             for (int r = 0; r < ROWS; ++r) {
-                const uint32_t e0 = uint32_t(r * NCW + ct) * 4;
-                const uint4 q = *reinterpret_cast<const uint4 *>(buf + e0);
-                v[r][0] = q.x * a.mul;
-                v[r][1] = q.y * a.mul;
-                v[r][2] = q.z * a.mul;
-                v[r][3] = q.w * a.mul;
-                uint32_t mk = pred_mask4(a.pred, v[r][0], v[r][1], v[r][2], v[r][3]);
-                if (valid != uint32_t(T)) {
-                    const uint32_t left = valid > e0 ? valid - e0 : 0u;
-                    mk &= left >= 4 ? 0xFu : ((1u << left) - 1u);
-                }
-                m[r] = mk;
-                packed += __popc(mk) << (8 * r);
+                const uint32_t e0 = uint32_t(r * 128 + lane * 4);
+                const uint4 q = *reinterpret_cast<const uint4 *>(seg + e0);
+                v[r][0] = q.x;
+                v[r][1] = q.y;
+                v[r][2] = q.z;
+                v[r][3] = q.w;
             }
-            const uint32_t incl = warp_incl_scan(packed, lane);
-            const uint32_t lane_excl = incl - packed;
-            if (lane == 31) s_wtot[cw] = incl;
-            bar_sync(1, NCW);  // every entry of the stage is in registers; warp totals are in
-            if (cw == 0) {
-                const uint64_t wt = lane < CWW ? spread8to16(s_wtot[lane]) : 0ull;
-                const uint64_t wi = warp_incl_scan64(wt, lane, CWW);
-                if (lane < CWW) s_wexcl[lane] = wi - wt;
-                const uint64_t total = __shfl_sync(kFull, wi, CWW - 1);  // inclusive total of the last warp
-                const uint32_t agg = uint32_t(total & 0xFFFFu) + uint32_t((total >> 16) & 0xFFFFu) +
-                                     uint32_t((total >> 32) & 0xFFFFu) + uint32_t(total >> 48);
-                if (lane == 0) {
-                    st_relaxed_u64(status_at(agg_words, tile), pack_status(epoch, kFlagAggregate, agg));
-                    s_tot = total;
-                    s_agg[j & 3] = agg;
-                    s_kept[s] = agg;
-                }
+            if (mul != 1u) {
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) v[r][c] *= mul;
             }
-            bar_sync(1, NCW);
-            const uint64_t tot = s_tot;
-            const uint64_t wex = s_wexcl[cw];
-            uint32_t rowbase = 0;
-            const uint32_t dummy = uint32_t(T) + uint32_t(lane);  // per-lane scratch slot past the tile
 #pragma unroll
             for (int r = 0; r < ROWS; ++r) {
-                uint32_t off = rowbase + uint32_t((wex >> (16 * r)) & 0xFFFFu) + ((lane_excl >> (8 * r)) & 0xFFu);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint32_t keep = (m[r] >> q) & 1u;
-                    buf[keep ? off : dummy] = v[r][q];
-                    off += keep;
+                const uint32_t e0 = uint32_t(r * 128 + lane * 4);
+                uint32_t mk = pred_mask4(a.pred, v[r][0], v[r][1], v[r][2], v[r][3]);
+                if (vlo != 0u || vhi != uint32_t(kSeg)) {
+                    const uint32_t skip = vlo > e0 ? min(vlo - e0, 4u) : 0u;
+                    const uint32_t left = vhi > e0 ? vhi - e0 : 0u;
+                    mk &= (0xFu << skip) & (left >= 4 ? 0xFu : ((1u << left) - 1u));
                 }
-                rowbase += uint32_t((tot >> (16 * r)) & 0xFFFFu);
+                m[r] = mk;
+                packed += uint32_t(__popc(mk)) << (8 * r);
             }
-            bar_arrive(kCountBar + int(j & 3), BLOCK);  // hand the count to the look-back warp
-        }
-    }
-    // Every issued copy has been consumed unless a wait gave up; drain those
-    // (bounded) so no copy lands after the block has exited.
-    if (ct == 0) {
-        const uint32_t pend = s_pending;
-        for (int s = 0; s < S; ++s) {
-            if (!((pend >> s) & 1u)) continue;
-            const uint32_t parity = (s_pend_j[s] / S) & 1u;
-            for (uint32_t polls = 0; polls < kMbarSpin; ++polls)
-                if (mbar_try_wait(&mbar[s], parity)) break;
+            // per-row counts, 8 bits each (a row of the warp keeps at most 128)
+            const uint32_t incl = warp_incl_scan(packed, lane);
+            const uint32_t excl = incl - packed;
+            const uint32_t rows = __shfl_sync(kFull, incl, 31);
+            __syncwarp();  // every lane holds its entries before any is overwritten
+            uint32_t rowbase = 0;
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                uint32_t pos = rowbase + ((excl >> (8 * r)) & 0xFFu);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if ((m[r] >> c) & 1u) seg[pos++] = v[r][c];
+                }
+                rowbase += (rows >> (8 * r)) & 0xFFu;
+            }
+            if (lane == 0) {
+                s_wcnt[k][w] = rowbase;
+                // the last segment counted publishes the tile aggregate at once
+                const uint32_t prev = atomicAdd(&s_pack[k], (1u << 16) | rowbase);
+                if ((prev >> 16) == uint32_t(CWW - 1)) {
+                    s_pack[k] = 0;
+                    st_relaxed_u64(status_at(agg_words, tile),
+                                   pack_status(epoch, kFlagAggregate, (prev & 0xFFFFu) + rowbase));
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&count_bar[k]);
         }
     }
 }
 
 namespace {
 
-template <int CWW, int S, int PF, int MAXG, int MINB>
+template <int CWW, int S, int LAG, int MAXG, int MINB>
 ka_status launch_tma_shape(const TmaArgs &a, uint64_t cap, cudaStream_t stream) {
-    constexpr int BLOCK = (CWW + 1) * 32, T = CWW * 32 * 16;
-    const size_t smem = size_t(S) * (T + 32) * 4;
-    auto kern = k_compact_tma<CWW, S, PF, MAXG, MINB>;
+    constexpr int BLOCK = (CWW + 2) * 32, T = CWW * kSeg;
+    const size_t smem = size_t(S) * T * 4;
+    auto kern = k_compact_tma<CWW, S, LAG, MAXG, MINB>;
     static int grid_cached = 0;
     if (grid_cached == 0) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
@@ -463,14 +431,19 @@ ka_status launch_tma_shape(const TmaArgs &a, uint64_t cap, cudaStream_t stream) 
 
 }  // namespace
 
+bool tma_shape(uint32_t block, uint32_t ipt) {
+    return ipt == 16 && (block == 256 || block == 512 || block == 768);
+}
+
 bool compact_tma_eligible(const CompactLaunch &L) {
-    if ((reinterpret_cast<uintptr_t>(L.in) & 15u) != 0) return false;
-    return L.tile.ipt == 16 && (L.tile.block == 256 || L.tile.block == 512);
+    // the shifted length n + lead must fit 32 bits
+    return tma_shape(L.tile.block, L.tile.ipt) && L.n <= 0xFFFFFFFCull;
 }
 
 ka_status launch_compact_tma(const CompactLaunch &L, cudaStream_t stream) {
     TmaArgs a;
-    a.in = L.in;
+    a.lead = uint32_t(reinterpret_cast<uintptr_t>(L.in) & 15u) / 4u;
+    a.in = L.in - a.lead;
     a.out = L.out;
     a.n_ptr = L.n_ptr;
     a.count = L.count;
@@ -480,8 +453,12 @@ ka_status launch_compact_tma(const CompactLaunch &L, cudaStream_t stream) {
     a.status_cap = status_capacity(L.ws_bytes);
     a.mul = L.mul;
     a.pred = L.pred;
-    if (L.tile.block == 512) return launch_tma_shape<16, 3, 2, 320, 2>(a, L.n, stream);
-    return launch_tma_shape<8, 4, 4, 480, 3>(a, L.n, stream);
+    // tile (768, 16): 24 compute warps, 12288 entries, 4 stages of 48 KiB, 1 block per SM;
+    // tile (512, 16): 16 compute warps, 8192 entries, 3 stages of 32 KiB, 2 blocks per SM;
+    // tile (256, 16): 8 compute warps, 4096 entries, 4 stages of 16 KiB, 3 blocks per SM.
+    if (L.tile.block == 768) return launch_tma_shape<24, 4, 3, 160, 1>(a, L.n + a.lead, stream);
+    if (L.tile.block == 512) return launch_tma_shape<16, 3, 2, 320, 2>(a, L.n + a.lead, stream);
+    return launch_tma_shape<8, 4, 2, 480, 3>(a, L.n + a.lead, stream);
 }
 
 }  // namespace ka

@@ -900,7 +900,8 @@ ka_status ka_spawn_stage(ka_system *h, const ka_stage_desc *d, ka_actor **out) {
     sp.kind = d->kind;
     sp.tile = d->tile;
     if (d->tile.block || d->tile.ipt) {
-        if (!tile_supported(d->tile.block, d->tile.ipt)) return KA_E_ARG;
+        const int32_t kernel = d->kind == KA_STAGE_EXSCAN ? KA_KERNEL_SCAN : KA_KERNEL_COMPACT;
+        if (!tile_supported_for(kernel, d->tile.block, d->tile.ipt)) return KA_E_ARG;
     }
     switch (d->kind) {
     case KA_STAGE_GENERATE: sp.in_arity = 0; sp.out_arity = 1; break;

@@ -1,7 +1,8 @@
-"""The warp-specialised TMA compaction (16-byte-aligned input, tile shapes
-(256, 16) and (512, 16)) against the oracle, bit for bit: ragged tails, live
-lengths from a device word, in place, hash transform, empty input, repeated
-launches on one workspace, and the full N = 2^28 workload at 1 %, 50 %, 99 %."""
+"""The warp-specialised TMA compaction (tile shapes (256, 16), (512, 16) and
+(768, 16)) against the oracle, bit for bit: ragged tails, inputs and outputs
+at every 4-byte offset, live lengths from a device word, in place, hash
+transform, empty input, repeated launches on one workspace, and the full
+N = 2^28 workload at 1 %, 50 %, 99 %."""
 import numpy as np
 import pytest
 
@@ -12,7 +13,7 @@ import ka_inputs as ki  # noqa: E402
 import oracle  # noqa: E402
 from gpu_util import SENTINEL, Workspace, empty, stream, to_dev, to_host, word  # noqa: E402
 
-TMA_SHAPES = [(512, 16), (256, 16)]
+TMA_SHAPES = [(768, 16), (512, 16), (256, 16)]
 
 
 @pytest.fixture(scope="module")
@@ -35,8 +36,8 @@ def compact(ka, d_x, n, pred, param, shape, xform=0, d_n=None, out=None, cap=Non
 
 
 @pytest.mark.parametrize("shape", TMA_SHAPES)
-@pytest.mark.parametrize("n", [1, 4095, 4096, 8191, 8192, 8193, 3 * 8192 + 5, 1 << 20, (1 << 22) + 12345,
-                               (1 << 23) + 1])
+@pytest.mark.parametrize("n", [1, 4095, 4096, 8191, 8192, 8193, 3 * 8192 + 5, 12287, 12288, 12289, 3 * 12288 + 5,
+                               1 << 20, (1 << 22) + 12345, (1 << 23) + 1])
 def test_tma_sizes(ka, shape, n):
     x = ki.uniform_u32(n + 7, n)
     out, k = compact(ka, to_dev(x), n, "lt", ki.threshold_for(0.37), shape)
@@ -96,6 +97,34 @@ def test_tma_unaligned_output(ka, shape, out_off):
 
 
 @pytest.mark.parametrize("shape", TMA_SHAPES)
+@pytest.mark.parametrize("in_off", [1, 2, 3])
+def test_tma_unaligned_input(ka, shape, in_off):
+    """Input views starting 4, 8 or 12 bytes past a 16-byte boundary: the tiles
+    are shifted back to the boundary and the lead entries belong to no tile."""
+    T = shape[0] * shape[1]
+    for n in [1, 2, 3, 5, T - in_off, T - in_off + 1, T, 3 * T + 7, (1 << 21) + 3]:
+        x = ki.uniform_u32(70 + in_off, n + in_off)
+        buf = to_dev(x, pad=16)
+        out, k = compact(ka, buf[in_off:], n, "lt", ki.threshold_for(0.55), shape)
+        y, ek = oracle.compact(x[in_off:], "lt", ki.threshold_for(0.55))
+        assert k == ek and np.array_equal(to_host(out, k), y), (n, in_off)
+        assert np.all(to_host(out)[k:n + 16] == SENTINEL)
+    # live length from a device word, hash transform, and in place, all unaligned
+    n = (1 << 21) + 99
+    x = ki.uniform_u32(80 + in_off, n + in_off)
+    live = n - 1000
+    d_n = to_dev(np.array([live], dtype=np.uint32))
+    out, k = compact(ka, to_dev(x)[in_off:], n, "popc_odd", 0, shape, xform=1, d_n=d_n)
+    y, ek = oracle.compact(oracle.map_hash(x[in_off:in_off + live]), "popc_odd", 0)
+    assert k == ek and np.array_equal(to_host(out, k), y)
+    d = to_dev(x)
+    out, k = compact(ka, d[in_off:], n, "ne", 0, shape, out=d[in_off:])
+    y, ek = oracle.compact(x[in_off:], "ne", 0)
+    assert k == ek and np.array_equal(to_host(d)[in_off:in_off + k], y)
+    assert np.array_equal(to_host(d)[:in_off], x[:in_off])
+
+
+@pytest.mark.parametrize("shape", TMA_SHAPES)
 def test_tma_workspace_reuse_and_shape_mix(ka, shape):
     ws = Workspace(ka, 1 << 22, (128, 4))  # sized for the smallest tile: fits every shape
     for i in range(30):
@@ -107,15 +136,16 @@ def test_tma_workspace_reuse_and_shape_mix(ka, shape):
         assert k == ek and np.array_equal(to_host(out, k), y), (i, n, sh)
 
 
+@pytest.mark.parametrize("shape", [(768, 16), (512, 16)])
 @pytest.mark.parametrize("s", [0.01, 0.5, 0.99])
-def test_full_size_2_28(ka, s):
+def test_full_size_2_28(ka, s, shape):
     """The benchmark workload itself: N = 2^28 generated on the device (seed 2),
-    keep x < floor(s 2^32), default (autotunable) shape; every output checked."""
+    keep x < floor(s 2^32), the large-input shapes; every output checked."""
     n = 1 << 28
     x_dev = torch.empty(n, dtype=torch.int32, device="cuda")
     assert ka.ka_generate(x_dev, n, 2, stream()) == 0
     t = ki.threshold_for(s)
-    out, k = compact(ka, x_dev, n, "lt", t, (512, 16))
+    out, k = compact(ka, x_dev, n, "lt", t, shape)
     del x_dev
     x = oracle.generate(2, n)
     y, ek = oracle.compact(x, "lt", t)
