@@ -39,7 +39,8 @@ SELECTIVITIES = (0.01, 0.5, 0.99)
 SEED = 2
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1709_07781_gb300", "csrc", f)
-                  for f in ("k_compact.cu", "ka_dev.cuh")]
+                  for f in ("k_compact_tma.cu", "ka_dev.cuh")]
+TMA_SHAPES = ((256, 16), (512, 16), (768, 16))
 
 
 def parse_args():
@@ -184,14 +185,14 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(tile):
     """Per-launch DRAM bytes of the fused kernel from the committed ncu summary,
-    only if it was taken on the current kernel source."""
+    only if it was taken on the current kernel source with the same tile."""
     try:
         with open(PROFILE_TRAFFIC) as fh:
             d = json.load(fh)
-        entry = d["k_compact_fused"]
-        if entry.get("source_sha") != kernel_source_sha():
+        entry = d["k_compact_tma"]
+        if entry.get("source_sha") != kernel_source_sha() or list(entry.get("tile", [])) != list(tile):
             return None
         return entry
     except Exception:
@@ -273,9 +274,10 @@ def run_ours(args):
     bytes_per_launch = [4.0 * N + 4.0 * kk for kk in kept]
     avg_launch_s = sum(per_sel_ms) / 3 / 1000.0
     achieved = (sum(bytes_per_launch) / 3) / avg_launch_s / 1e9
-    traffic = profiled_traffic()
+    tma = tuple(tile) in TMA_SHAPES
+    traffic = profiled_traffic(tile) if tma else None
     roofline = {
-        "kernel": "k_compact_fused<%d,%d>" % tuple(tile),
+        "kernel": ("k_compact_tma<%d,%d>" if tma else "k_compact_fused<%d,%d>") % tuple(tile),
         "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
         "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
         "traffic": (traffic["bytes_per_launch_avg"] if traffic else None),
@@ -294,7 +296,7 @@ def run_ours(args):
                                % (N.bit_length() - 1),
                    "n": N, "selectivities": list(SELECTIVITIES), "kept": kept, "tile": list(tile),
                    "tile_source": tile_source,
-                   "l2": "inputs (1 GiB) larger than L2; no flush", "parallelism": "replicas x%d" % world},
+                   "l2": "inputs (%.2f GiB) larger than L2; no flush" % (N * 4 / 2**30), "parallelism": "replicas x%d" % world},
         "roofline": roofline, "gpu_launches": launches, "clocks": clock_info,
         "device_status": ka.ka_strerror(dev_status), "valid": dev_status == 0,
     }
@@ -303,6 +305,15 @@ def run_ours(args):
         result["e2e"] = e2e_large(ka, torch, x, kept, thresholds, ws, ws_bytes, D, min(K, 10))
     if not args.no_extras:
         result["extras"] = {"three_launch": three_launch_large(ka, torch, x, thresholds, D, peak)}
+        del x, out
+        torch.cuda.empty_cache()
+        result["extras"]["actor_vs_direct"] = actor_overhead(ka, torch)
+        result["extras"]["batch_4096"] = batch_large(ka, torch, peak)
+        result["extras"]["serve"] = serve_large(ka, torch)
+        sv = result["extras"]["serve"][0]
+        result["latency"] = {"workload": "serving loop, Poisson %d requests/s" % sv["rate_per_s"],
+                             "batched_p50_ms": sv["batched"]["p50_ms"], "batched_p99_ms": sv["batched"]["p99_ms"],
+                             "plain_p50_ms": sv["plain"]["p50_ms"], "plain_p99_ms": sv["plain"]["p99_ms"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline_large(kept, N)
     D.close()
@@ -394,6 +405,202 @@ def three_launch_large(ka, torch, x, thresholds, D, peak):
                                         "GB/s": round(bytes_[kname] / (tv / 1000) / 1e9, 1),
                                         "frac": round(bytes_[kname] / (tv / 1000) / 1e9 / peak, 4)}
                                 for kname, tv in times.items()}})
+    return out
+
+
+def actor_overhead(ka, torch):
+    """The actor path (request/receive through mailbox and dispatcher) against
+    the same kernels launched directly, one pipeline after another, each
+    waiting for its result count on the host: the 3-actor pipeline (N = 2^20,
+    keep (x & 3) == 0), its fused single-actor form, and the 4-stage pipeline
+    (N = 2^26: hash, keep top bits < 8, keep popc odd, keep % 3 != 0)."""
+    import ka_inputs as ki
+    P = ka.PRED
+    cases = [
+        ("3-actor predicate/scan/scatter N=2^20", 1 << 20, 1, 2000,
+         [(ka.KA_STAGE_PREDICATE, P["and_mask_eq0"], 3, 0), (ka.KA_STAGE_EXSCAN, 0, 0, 0),
+          (ka.KA_STAGE_SCATTER, 0, 0, 0)]),
+        ("fused compaction actor N=2^20", 1 << 20, 1, 2000,
+         [(ka.KA_STAGE_COMPACT, P["and_mask_eq0"], 3, 0)]),
+        ("4-stage pipeline N=2^26 (hash fused into stage 2)", 1 << 26, 3, 200,
+         [(ka.KA_STAGE_COMPACT, P["topbits_lt"], 8, ka.KA_XFORM_HASH), (ka.KA_STAGE_COMPACT, P["popc_odd"], 0, 0),
+          (ka.KA_STAGE_COMPACT, P["mod_ne0"], 3, 0)]),
+        ("4-stage pipeline N=2^26 (hash as its own actor)", 1 << 26, 3, 200,
+         [(ka.KA_STAGE_MAP_HASH, 0, 0, 0), (ka.KA_STAGE_COMPACT, P["topbits_lt"], 8, 0),
+          (ka.KA_STAGE_COMPACT, P["popc_odd"], 0, 0), (ka.KA_STAGE_COMPACT, P["mod_ne0"], 3, 0)]),
+    ]
+    s, sysh = ka.ka_system_create(0)
+    ka.check(s)
+    out = []
+    try:
+        for name, n, seed, iters, specs in cases:
+            x = torch.empty(n, dtype=torch.int32, device="cuda")
+            ka.check(ka.ka_generate(x, n, seed, torch.cuda.current_stream().cuda_stream))
+            torch.cuda.synchronize()
+            actors = []
+            for kind, pred, param, xform in specs:
+                s, a = ka.ka_spawn_stage(sysh, kind, pred, param, xform)
+                ka.check(s)
+                actors.append(a)
+            pipe = actors[0]
+            for nxt in actors[1:]:
+                s, pipe = ka.ka_compose(nxt, pipe)
+                ka.check(s)
+            s, ref = ka.ka_ref_wrap(sysh, x, n, n)
+            ka.check(s)
+            msg = ka.make_msg(refs=[ref])
+            ka.check(ka.ka_bench_request_loop(pipe, msg, 20, 1)[0])  # warm-up (pool, autotune table)
+            s, t_actor, k_actor = ka.ka_bench_request_loop(pipe, msg, iters, 1)
+            ka.check(s)
+            s, t_direct, k_direct = ka.ka_bench_direct_chain(specs, x, n, iters)
+            ka.check(s)
+            us_a, us_d = t_actor / iters * 1e6, t_direct / iters * 1e6
+            out.append({"pipeline": name, "n": n, "iters": iters, "actor_us": round(us_a, 2),
+                        "direct_us": round(us_d, 2), "overhead_pct": round(100.0 * (us_a / us_d - 1.0), 2),
+                        "actor_elements/s": n / (us_a * 1e-6), "count": int(k_actor),
+                        "counts_match": int(k_actor) == int(k_direct)})
+            ka.ka_ref_release(ref)
+            for a in ([pipe] if len(actors) > 1 else []) + actors:
+                ka.ka_actor_release(a)
+            del x
+    finally:
+        ka.ka_system_destroy(sysh, 1)
+    return out
+
+
+def batch_large(ka, torch, peak):
+    """4096 independent compactions (sizes log-uniform 2^8..2^20, thresholds
+    for selectivities U[1 %, 99 %)) in one persistent launch, replayed from a
+    captured CUDA graph, against the same instances as 4096 separate launches."""
+    import numpy as np
+    import ka_inputs as ki
+    spec = ki.config_batch()
+    m = len(spec.n)
+    n = spec.n.astype(np.int64)
+    offs = np.concatenate([[0], np.cumsum((n + 3) // 4 * 4)])  # 16-byte aligned instances
+    total = int(offs[-1])
+    st = torch.cuda.current_stream()
+    x = torch.empty(total, dtype=torch.int32, device="cuda")
+    y = torch.empty(total, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(m, dtype=torch.int32, device="cuda")
+    cnt2 = torch.zeros(m, dtype=torch.int32, device="cuda")
+    xb, yb, cb = x.data_ptr(), y.data_ptr(), cnt.data_ptr()
+    gen = (ka.ka_gen_item * m)()
+    items = (ka.ka_batch_item * m)()
+    for i in range(m):
+        gen[i] = ka.ka_gen_item(xb + 4 * int(offs[i]), int(spec.seeds[i]), int(n[i]), 0)
+        items[i] = ka.ka_batch_item(xb + 4 * int(offs[i]), yb + 4 * int(offs[i]), None, cb + 4 * i, int(n[i]),
+                                    ka.KA_PRED_LT, int(spec.t[i]), 0)
+    d_gen = torch.frombuffer(bytearray(bytes(gen)), dtype=torch.uint8).cuda()
+    d_items = torch.frombuffer(bytearray(bytes(items)), dtype=torch.uint8).cuda()
+    s, tile = ka.ka_tile_for(ka.KA_KERNEL_BATCH, 1 << 17)
+    ka.check(s)
+    s, wsb = ka.ka_batch_workspace_size(m, total, tile)
+    ka.check(s)
+    ws_t = torch.empty(wsb + 256, dtype=torch.uint8, device="cuda")
+    ws = (ws_t.data_ptr() + 255) // 256 * 256
+    ka.check(ka.ka_workspace_init(ws, wsb, st.cuda_stream))
+    ka.check(ka.ka_generate_batch(d_gen, m, m, ws, wsb, st.cuda_stream))
+
+    def batched(stream):
+        ka.check(ka.ka_compact_batch(d_items, m, m, ws, wsb, tile, 0, stream))
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1000.0 / reps
+
+    us_launch = timed(lambda: batched(st.cuda_stream), 20)
+    g = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream()
+    cap.wait_stream(st)
+    with torch.cuda.stream(cap):
+        batched(cap.cuda_stream)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=cap):
+            batched(cap.cuda_stream)
+    torch.cuda.synchronize()
+    us_graph = timed(g.replay, 20)
+    kept = cnt.cpu().numpy().view(np.uint32).astype(np.int64)
+    # the same instances as separate launches of the single-array kernel
+    s, wsb1 = ka.ka_workspace_size(int(n.max()))
+    ka.check(s)
+    ws1_t = torch.empty(wsb1 + 256, dtype=torch.uint8, device="cuda")
+    ws1 = (ws1_t.data_ptr() + 255) // 256 * 256
+    ka.check(ka.ka_workspace_init(ws1, wsb1, st.cuda_stream))
+    c2 = cnt2.data_ptr()
+
+    def separate():
+        for i in range(m):
+            ka.check(ka.ka_compact(xb + 4 * int(offs[i]), int(n[i]), None, ka.KA_PRED_LT, int(spec.t[i]), 0,
+                                   yb + 4 * int(offs[i]), c2 + 4 * i, ws1, wsb1, None, st.cuda_stream))
+
+    us_sep = timed(separate, 3)
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(cap):
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g2, stream=cap):
+            for i in range(m):
+                ka.check(ka.ka_compact(xb + 4 * int(offs[i]), int(n[i]), None, ka.KA_PRED_LT, int(spec.t[i]), 0,
+                                       yb + 4 * int(offs[i]), c2 + 4 * i, ws1, wsb1, None, cap.cuda_stream))
+    torch.cuda.synchronize()
+    us_sep_graph = timed(g2.replay, 5)
+    kept2 = cnt2.cpu().numpy().view(np.uint32).astype(np.int64)
+    elems = int(n.sum())
+    alg = float(4 * n.sum() + 4 * kept.sum())
+
+    def rec(us):
+        return {"us": round(us, 1), "elements/s": elems / (us * 1e-6),
+                "GB/s": round(alg / (us * 1e-6) / 1e9, 1), "frac": round(alg / (us * 1e-6) / 1e9 / peak, 4)}
+    return {"instances": m, "elements": elems, "kept": int(kept.sum()), "tile": list(tile),
+            "batched_launch": rec(us_launch), "batched_graph_replay": rec(us_graph),
+            "separate_launches": rec(us_sep), "separate_graph_replay": rec(us_sep_graph),
+            "counts_match": bool(np.array_equal(kept, kept2))}
+
+
+def serve_large(ka, torch):
+    """The serving loop on Poisson traces (requests of 1-4 stages from the
+    4-stage set over fresh seeded arrays, n log-uniform 2^10..2^24, budget
+    64 GiB): continuous batching against plain per-request launches, at the
+    nominal 20 000 requests/s and at a saturating 80 000 requests/s."""
+    import numpy as np
+    import ka_inputs as ki
+    s, sysh = ka.ka_system_create(0, budget_bytes=64 << 30)
+    ka.check(s)
+
+    def spec(stg):
+        return ((ka.PRED["all"], 0, ka.KA_XFORM_HASH) if stg.kind == "map_hash"
+                else (ka.PRED[stg.pred], stg.param, ka.KA_XFORM_NONE))
+    out = []
+    try:
+        for rate, dur in ((20000.0, 1.0), (80000.0, 0.5)):
+            tr = ki.config_serve(rate, dur)
+            stages = [[spec(ki.PIPELINE4[int(k)]) for k in tr.stage_kind[r][:tr.n_stages[r]]]
+                      for r in range(len(tr.n))]
+            reqs = ka.serve_requests(tr.arrival_s, tr.n, tr.seeds, stages)
+            row = {"rate_per_s": rate, "duration_s": dur, "requests": len(tr.n),
+                   "offered_elements/s": float(np.sum(tr.n)) / dur}
+            for mode, name in ((0, "batched"), (1, "plain")):
+                s, res, stats = ka.serve(sysh, reqs, mode=mode)
+                ka.check(s)
+                lat = np.array([res[r].done_s - tr.arrival_s[r] for r in range(len(tr.n))])
+                row[name] = {"elements/s": stats.elements / stats.wall_s, "wall_s": round(stats.wall_s, 4),
+                             "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
+                             "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
+                             "p999_ms": round(1e3 * float(np.percentile(lat, 99.9)), 3),
+                             "launches": int(stats.launches), "iterations": int(stats.iterations),
+                             "peak_GB": round(stats.peak_bytes / 1e9, 3),
+                             "ok": all(res[r].status == 0 for r in range(len(tr.n)))}
+            out.append(row)
+    finally:
+        ka.ka_system_destroy(sysh, 1)
     return out
 
 

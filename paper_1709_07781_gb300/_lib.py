@@ -456,6 +456,33 @@ def ka_serve_run(sys_h, reqs, n_reqs: int, opt, results, stats) -> int:
     return lib.ka_serve_run(sys_h, reqs, n_reqs, ctypes.byref(opt), results, ctypes.byref(stats))
 
 
+def serve_requests(arrival_s, n, seeds, stages):
+    """Request array for ka_serve_run. stages[r] = [(pred, param, xform), ...]
+    (1-4 entries) for request r."""
+    arr = (ka_serve_request * len(n))()
+    for r in range(len(n)):
+        q = arr[r]
+        q.arrival_s = float(arrival_s[r])
+        q.seed = int(seeds[r]) & (2**64 - 1)
+        q.n = int(n[r])
+        q.n_stages = len(stages[r])
+        for i, (pred, param, xform) in enumerate(stages[r]):
+            q.stages[i] = ka_serve_stage(int(pred), int(param) & 0xFFFFFFFF, int(xform))
+        q.h_out = None
+        q.h_out_cap = 0
+    return arr
+
+
+def serve(sys_h, reqs, mode: int = 0, budget_bytes: int = 0, max_inflight: int = 0, time_scale: float = 1.0,
+          tile=None):
+    """Runs ka_serve_run; returns (status, results array, stats)."""
+    opt = ka_serve_options(mode, max_inflight, budget_bytes, time_scale, ka_tile(*(tile or (0, 0))))
+    results = (ka_serve_result * max(len(reqs), 1))()
+    stats = ka_serve_stats()
+    st = lib.ka_serve_run(sys_h, reqs, len(reqs), ctypes.byref(opt), results, ctypes.byref(stats))
+    return st, results, stats
+
+
 def ka_bench_request_loop(actor_h, msg: ka_msg, iters: int, inflight: int = 1):
     sec, last = ctypes.c_double(0), ctypes.c_uint64(0)
     s = lib.ka_bench_request_loop(actor_h, ctypes.byref(msg), iters, inflight, ctypes.byref(sec), ctypes.byref(last))

@@ -52,6 +52,9 @@ inline uint32_t status_capacity(uint64_t ws_bytes) {
     return e > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(e);
 }
 
+// Device ordinal and memory budget of an actor system (for the serving loop).
+ka_status system_exec_info(ka_system *sys, int *device, uint64_t *budget);
+
 // Launchers shared by the C ABI and the actor runtime. All asynchronous.
 struct CompactLaunch {
     const uint32_t *in;

@@ -691,6 +691,15 @@ static void request_free(Request *r) {
 }
 
 }  // namespace rt
+
+ka_status system_exec_info(ka_system *h, int *device, uint64_t *budget) {
+    rt::System *s = rt::sys_of(h);
+    if (!s) return KA_E_STALE;
+    *device = s->device;
+    *budget = s->budget;
+    return KA_OK;
+}
+
 }  // namespace ka
 
 using namespace ka;
