@@ -493,7 +493,7 @@ def batch_large(ka, torch, peak):
                                     ka.KA_PRED_LT, int(spec.t[i]), 0)
     d_gen = torch.frombuffer(bytearray(bytes(gen)), dtype=torch.uint8).cuda()
     d_items = torch.frombuffer(bytearray(bytes(items)), dtype=torch.uint8).cuda()
-    s, tile = ka.ka_tile_for(ka.KA_KERNEL_BATCH, 1 << 17)
+    s, tile, tuned_us = ka.ka_autotune(ka.KA_KERNEL_BATCH, total, None, st.cuda_stream)
     ka.check(s)
     s, wsb = ka.ka_batch_workspace_size(m, total, tile)
     ka.check(s)
@@ -560,6 +560,7 @@ def batch_large(ka, torch, peak):
         return {"us": round(us, 1), "elements/s": elems / (us * 1e-6),
                 "GB/s": round(alg / (us * 1e-6) / 1e9, 1), "frac": round(alg / (us * 1e-6) / 1e9 / peak, 4)}
     return {"instances": m, "elements": elems, "kept": int(kept.sum()), "tile": list(tile),
+            "tile_source": "autotuned on a synthetic batch (%.1f us)" % tuned_us,
             "batched_launch": rec(us_launch), "batched_graph_replay": rec(us_graph),
             "separate_launches": rec(us_sep), "separate_graph_replay": rec(us_sep_graph),
             "counts_match": bool(np.array_equal(kept, kept2))}

@@ -248,6 +248,11 @@ ka_status ka_generate_batch(const ka_gen_item *d_items, uint32_t n_items, uint32
 #define KA_KERNEL_COMPACT 0
 #define KA_KERNEL_SCAN    1
 #define KA_KERNEL_BATCH   2
+/* COMPACT and SCAN: one array of n entries, keep x < 2^31. BATCH: a synthetic
+ * batch of at most 4096 instances with sizes log-uniform in 2^8..2^20 and
+ * n entries in total; its result applies to every batch (ka_compact_batch
+ * looks up one entry). Allocates its inputs with cudaMalloc and synchronises
+ * `stream`; do not call it during a stream capture. */
 ka_status ka_autotune(int32_t kernel, uint64_t n, const char *cache_path, ka_tile *best,
                       float *best_us, void *stream);
 /* Shape the library uses for (kernel, n) now (default or autotuned). */

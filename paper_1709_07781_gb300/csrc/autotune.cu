@@ -138,6 +138,77 @@ static float time_launches(F launch, cudaStream_t st, int warm, int reps) {
     return t[t.size() / 2];
 }
 
+// Batch shape search: a synthetic batch (sizes log-uniform in 2^8..2^20 from
+// a fixed SplitMix64 stream, each instance 16-byte aligned, keep x < 2^31),
+// every shape timed on it; the winner is stored under the bucket that
+// ka_compact_batch looks up.
+ka_status autotune_batch(uint64_t total, const char *cache_path, ka_tile *best, float *best_us, void *stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<uint32_t> sizes;
+    uint64_t sum = 0, z = 0x5EEDull;
+    while (sum < total && sizes.size() < 4096) {
+        z += 0x9E3779B97F4A7C15ull;
+        uint64_t m = z;
+        m = (m ^ (m >> 30)) * 0xBF58476D1CE4E5B9ull;
+        m = (m ^ (m >> 27)) * 0x94D049BB133111EBull;
+        m ^= m >> 31;
+        const double u = double(m >> 11) * (1.0 / 9007199254740992.0);
+        uint32_t sz = uint32_t(std::pow(2.0, 8.0 + 12.0 * u));
+        sz = std::min<uint64_t>(sz, total - sum);
+        sizes.push_back(sz);
+        sum += sz;
+    }
+    const uint32_t m = uint32_t(sizes.size());
+    std::vector<uint64_t> off(m + 1, 0);
+    for (uint32_t i = 0; i < m; ++i) off[i + 1] = off[i] + (uint64_t(sizes[i]) + 3) / 4 * 4;
+    uint32_t *in = nullptr, *out = nullptr, *count = nullptr;
+    ka_batch_item *d_items = nullptr;
+    void *ws = nullptr;
+    uint64_t ws_bytes = 0;
+    ka_status s = ka_batch_workspace_size(m, off[m], nullptr, &ws_bytes);  // sized for the smallest tile
+    if (s == KA_OK &&
+        (cudaMalloc(&in, off[m] * 4 + 16) != cudaSuccess || cudaMalloc(&out, off[m] * 4 + 16) != cudaSuccess ||
+         cudaMalloc(&count, size_t(m) * 4) != cudaSuccess ||
+         cudaMalloc(&d_items, sizeof(ka_batch_item) * m) != cudaSuccess || cudaMalloc(&ws, ws_bytes) != cudaSuccess))
+        s = KA_E_OOM;
+    std::vector<ka_batch_item> items(m);
+    for (uint32_t i = 0; i < m; ++i)
+        items[i] = ka_batch_item{in + off[i], out + off[i], nullptr, count + i, sizes[i], KA_PRED_LT, 0x80000000u,
+                                 KA_XFORM_NONE};
+    if (s == KA_OK) s = launch_generate(in, off[m], 0xA5A5ull + total, nullptr, st);
+    if (s == KA_OK)
+        s = cuda_status(cudaMemcpyAsync(d_items, items.data(), sizeof(ka_batch_item) * m, cudaMemcpyHostToDevice, st));
+    if (s == KA_OK) s = ka_workspace_init(ws, ws_bytes, st);
+    ka_tile win{0, 0};
+    float win_us = 1e30f;
+    if (s == KA_OK) {
+        for (const ka_tile &t : kShapes) {
+            auto launch = [&]() -> ka_status { return ka_compact_batch(d_items, m, m, ws, ws_bytes, &t, 0, st); };
+            const float us = time_launches(launch, st, 2, 9);
+            if (us > 0 && us < win_us) {
+                win_us = us;
+                win = t;
+            }
+        }
+        if (win.block == 0) s = KA_E_CUDA;
+    }
+    cudaStreamSynchronize(st);
+    if (in) cudaFree(in);
+    if (out) cudaFree(out);
+    if (count) cudaFree(count);
+    if (d_items) cudaFree(d_items);
+    if (ws) cudaFree(ws);
+    if (s != KA_OK) return s;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        g_table[{KA_KERNEL_BATCH, bucket_of(kBatchTileKey)}] = {win, win_us};
+        if (cache_path) save_table(cache_path);
+    }
+    if (best) *best = win;
+    if (best_us) *best_us = win_us;
+    return KA_OK;
+}
+
 }  // namespace ka
 
 using namespace ka;
@@ -159,6 +230,7 @@ ka_status ka_autotune_load(const char *cache_path) {
 ka_status ka_autotune(int32_t kernel, uint64_t n, const char *cache_path, ka_tile *best, float *best_us,
                       void *stream) {
     if (n == 0 || n > 0xFFFFFFFFull) return KA_E_ARG;
+    if (kernel == KA_KERNEL_BATCH) return autotune_batch(n, cache_path, best, best_us, stream);
     if (kernel != KA_KERNEL_COMPACT && kernel != KA_KERNEL_SCAN) return KA_E_UNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint32_t *in = nullptr, *out = nullptr, *count = nullptr;

@@ -293,7 +293,7 @@ ka_status ka_compact_batch(const ka_batch_item *d_items, uint32_t n_items, uint3
     if (!d_ws || (reinterpret_cast<uintptr_t>(d_ws) & 255u) != 0) return KA_E_ARG;
     if (ws_bytes < batch_fixed_bytes(max_items) + kStatusEntryBytes) return KA_E_WORKSPACE;
     if (n_items == 0) return KA_OK;
-    const ka_tile t = resolve_tile(KA_KERNEL_BATCH, 1ull << 17, tile);
+    const ka_tile t = resolve_tile(KA_KERNEL_BATCH, kBatchTileKey, tile);
     if (!tile_supported(t.block, t.ipt)) return KA_E_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     BatchArgs a;

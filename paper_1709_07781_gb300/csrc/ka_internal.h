@@ -37,6 +37,9 @@ bool tma_shape(uint32_t block, uint32_t ipt);
 bool tile_supported_for(int32_t kernel, uint32_t block, uint32_t ipt);
 // Shape to use for `kernel` at size n: explicit shape, else autotuned, else default.
 ka_tile resolve_tile(int32_t kernel, uint64_t n, const ka_tile *requested);
+// The batch kernel has one shape for every batch, stored under this size.
+constexpr uint64_t kBatchTileKey = 1ull << 17;
+ka_status autotune_batch(uint64_t total, const char *cache_path, ka_tile *best, float *best_us, void *stream);
 
 // Workspace layout for single-pass kernels: the 256-byte header, then status
 // entries of kStatusStride words. Room for two entries per tile: one per tile

@@ -342,7 +342,7 @@ ka_status setup(Run &R, uint32_t max_n) {
     uint64_t keep = ~0ull;  // keep freed memory in the pool for the next requests
     cudaMemPoolSetAttribute(R.pool, cudaMemPoolAttrReleaseThreshold, &keep);
     if (R.mode == 0) {
-        R.batch_tile = resolve_tile(KA_KERNEL_BATCH, 1ull << 17, R.tile.block ? &R.tile : nullptr);
+        R.batch_tile = resolve_tile(KA_KERNEL_BATCH, kBatchTileKey, R.tile.block ? &R.tile : nullptr);
         R.grid_max = uint32_t(device_info().sm_count) * 8;
         s = ka_batch_workspace_size(kTickItems, 0, nullptr, &R.ws_gen_bytes);
         if (s == KA_OK)
