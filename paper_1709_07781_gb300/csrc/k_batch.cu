@@ -10,45 +10,10 @@
 // within a block), and run the fused tile body with a look-back that stops at
 // the item's first tile. Every status word is indexed by flattened tile, so
 // each item owns a contiguous segment of the status array.
-#include "ka_internal.h"
+#include "ka_batch.cuh"
 #include "ka_tile.cuh"
 
 namespace ka {
-
-struct ItemPlan {  // 32 bytes
-    PredDev pred;
-    uint32_t mul;
-    uint32_t n;
-    uint32_t tiles;
-};
-static_assert(sizeof(ItemPlan) == 32, "plan record is 32 bytes");
-
-struct BatchLayout {
-    uint32_t *tile_off;  // [max_items + 1]
-    ItemPlan *plans;     // [max_items]
-    uint64_t *status;    // [status_cap]
-    uint32_t status_cap;
-};
-
-static inline uint64_t round256(uint64_t b) { return (b + 255) / 256 * 256; }
-
-static uint64_t batch_fixed_bytes(uint32_t max_items) {
-    return kWsHeaderBytes + round256((uint64_t(max_items) + 1) * 4) + round256(uint64_t(max_items) * 32);
-}
-
-static BatchLayout batch_layout(void *ws, uint64_t ws_bytes, uint32_t max_items) {
-    BatchLayout L;
-    char *p = static_cast<char *>(ws) + kWsHeaderBytes;
-    L.tile_off = reinterpret_cast<uint32_t *>(p);
-    p += round256((uint64_t(max_items) + 1) * 4);
-    L.plans = reinterpret_cast<ItemPlan *>(p);
-    p += round256(uint64_t(max_items) * 32);
-    L.status = reinterpret_cast<uint64_t *>(p);
-    const uint64_t fixed = batch_fixed_bytes(max_items);
-    const uint64_t entries = ws_bytes > fixed ? (ws_bytes - fixed) / kStatusEntryBytes : 0;
-    L.status_cap = entries > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(entries);
-    return L;
-}
 
 constexpr int kPlanBlock = 1024;
 
@@ -71,8 +36,10 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp
     return r;
 }
 
+// With `shift`, an item's tiles cover its input shifted back to a 16-byte
+// boundary (the TMA kernel), so its lead entries count in its tile count.
 __global__ void __launch_bounds__(kPlanBlock) k_batch_plan(const ka_batch_item *items, uint32_t n_items,
-                                                            uint32_t T, BatchLayout L, WsHeader *ws) {
+                                                            uint32_t T, BatchLayout L, WsHeader *ws, bool shift) {
     __shared__ uint32_t s_warp[33];
     uint32_t carry = 0;
     for (uint32_t base = 0; base < n_items; base += kPlanBlock) {
@@ -93,7 +60,8 @@ __global__ void __launch_bounds__(kPlanBlock) k_batch_plan(const ka_batch_item *
             }
             pl.mul = it.xform == 1u ? kHashMul : 1u;
             pl.n = n;
-            tiles = uint32_t((uint64_t(n) + T - 1) / T);
+            const uint32_t lead = shift && n ? uint32_t(reinterpret_cast<uintptr_t>(it.in) & 15u) / 4u : 0u;
+            tiles = uint32_t((uint64_t(n) + lead + T - 1) / T);
             pl.tiles = tiles;
             L.plans[i] = pl;
             if (n == 0 && it.count) *it.count = 0u;
@@ -109,40 +77,6 @@ __global__ void __launch_bounds__(kPlanBlock) k_batch_plan(const ka_batch_item *
     }
 }
 
-// Item owning flattened tile `ticket`: the largest i with tile_off[i] <= ticket.
-// Precondition: tile_off[lo] <= ticket < tile_off[n_items]. Called by a full warp.
-__device__ __forceinline__ uint32_t find_item(const uint32_t *tile_off, uint32_t n_items, uint32_t lo,
-                                              uint32_t ticket) {
-    const int lane = threadIdx.x & 31;
-    {
-        const uint32_t j = lo + 1 + lane;
-        const uint32_t v = j <= n_items ? tile_off[j] : 0xFFFFFFFFu;
-        const uint32_t b = __ballot_sync(kFull, v > ticket);
-        if (b) return lo + __ffs(b) - 1;
-    }
-    lo += 32;
-    uint32_t hi = n_items;
-    while (hi - lo > 1) {
-        const uint32_t step = (hi - lo + 31) / 32;
-        const uint64_t jj = uint64_t(lo) + uint64_t(lane + 1) * step;
-        const uint32_t j = jj < hi ? uint32_t(jj) : hi;
-        const uint32_t v = tile_off[j];
-        const uint32_t b = __ballot_sync(kFull, v > ticket);
-        const uint32_t f = __ffs(b) - 1;
-        const uint64_t nh = uint64_t(lo) + uint64_t(f + 1) * step;
-        const uint32_t new_hi = nh < hi ? uint32_t(nh) : hi;
-        lo = f == 0 ? lo : lo + f * step;
-        hi = new_hi;
-    }
-    return lo;
-}
-
-struct BatchArgs {
-    const ka_batch_item *items;
-    uint32_t n_items;
-    BatchLayout L;
-    WsHeader *ws;
-};
 
 template <int BLOCK, int IPT>
 __global__ void __launch_bounds__(BLOCK) k_compact_batch(const BatchArgs a) {
@@ -278,10 +212,11 @@ ka_status ka_batch_workspace_size(uint32_t max_items, uint64_t total_capacity, c
     if (!bytes || max_items == 0) return KA_E_ARG;
     uint32_t te = 512;
     if (tile && tile->block && tile->ipt) {
-        if (!tile_supported(tile->block, tile->ipt)) return KA_E_ARG;
+        if (!tile_supported_for(KA_KERNEL_BATCH, tile->block, tile->ipt)) return KA_E_ARG;
         te = tile->block * tile->ipt;
     }
-    const uint64_t tiles = tiles_for(total_capacity, te) + max_items + 1;
+    // + 3 entries per item: the TMA shapes shift each item back to a 16-byte boundary
+    const uint64_t tiles = tiles_for(total_capacity + 3ull * max_items, te) + max_items + 1;
     *bytes = batch_fixed_bytes(max_items) + round256(tiles * kStatusEntryBytes);
     return KA_OK;
 }
@@ -294,16 +229,18 @@ ka_status ka_compact_batch(const ka_batch_item *d_items, uint32_t n_items, uint3
     if (ws_bytes < batch_fixed_bytes(max_items) + kStatusEntryBytes) return KA_E_WORKSPACE;
     if (n_items == 0) return KA_OK;
     const ka_tile t = resolve_tile(KA_KERNEL_BATCH, kBatchTileKey, tile);
-    if (!tile_supported(t.block, t.ipt)) return KA_E_ARG;
+    if (!tile_supported_for(KA_KERNEL_BATCH, t.block, t.ipt)) return KA_E_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     BatchArgs a;
     a.items = d_items;
     a.n_items = n_items;
     a.L = batch_layout(d_ws, ws_bytes, max_items);
     a.ws = static_cast<WsHeader *>(d_ws);
-    k_batch_plan<<<1, kPlanBlock, 0, st>>>(d_items, n_items, t.block * t.ipt, a.L, a.ws);
+    const bool tma = tma_shape(t.block, t.ipt);
+    k_batch_plan<<<1, kPlanBlock, 0, st>>>(d_items, n_items, t.block * t.ipt, a.L, a.ws, tma);
     ka_status s = cuda_status(cudaGetLastError());
     if (s != KA_OK) return s;
+    if (tma) return launch_batch_tma(a, t, grid, st);
     switch (shape_key(t.block, t.ipt)) {
 #define KA_CASE(B, I) \
     case shape_key(B, I): return launch_batch_shape<B, I>(a, grid, st);

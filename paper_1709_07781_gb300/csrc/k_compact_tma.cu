@@ -34,64 +34,12 @@
 // one barrier word serialise. Every wait is bounded (a few seconds); on
 // time-out the kernel records a device error and still finishes.
 #include "ka_internal.h"
+#include "ka_tma.cuh"
 
 namespace ka {
 namespace {
 
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *m) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(m)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *m, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_addr(m)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Waits until the phase of parity `parity` of m has completed. Gives up after
-// kWaitNs of wall time and returns false.
-constexpr uint64_t kWaitNs = 2000000000ull;
-__device__ __forceinline__ bool mbar_wait(uint64_t *m, uint32_t parity) {
-    if (mbar_try_wait(m, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (uint32_t i = 1;; ++i) {
-        if (mbar_try_wait(m, parity)) return true;
-        if ((i & 15u) == 0u && global_ns() - t0 > kWaitNs) return false;
-    }
-}
-
-// Bulk copy global -> this block's shared memory, completing on mbarrier m.
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *m) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(m))
-                 : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-constexpr int kSeg = 512;         // entries per compute warp and tile (32 lanes x 4 rows x 4)
+using namespace tma;
 
 struct TmaArgs {
     const uint32_t *in;  // input rounded down to 16 bytes: entry i of the input is in[lead + i]
@@ -106,46 +54,6 @@ struct TmaArgs {
     uint32_t lead;  // 0..3 entries before the input's first entry
     PredDev pred;
 };
-
-// One warp copies cnt compacted entries from shared memory (16-byte aligned)
-// to dst (4-byte aligned): single entries up to dst's next 16-byte boundary,
-// then 16-byte stores, each assembled from two aligned 16-byte shared loads,
-// then the remaining single entries. cnt <= kSeg.
-__device__ __forceinline__ void warp_copy_out(const uint32_t *src, uint32_t *dst, uint32_t cnt, int lane) {
-    const uint32_t to16 = uint32_t((16u - (reinterpret_cast<uintptr_t>(dst) & 15u)) & 15u) >> 2;
-    const uint32_t head = to16 < cnt ? to16 : cnt;
-    if (uint32_t(lane) < head) dst[lane] = src[lane];
-    const uint32_t body = (cnt - head) >> 2;
-    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
-    uint4 *d4 = reinterpret_cast<uint4 *>(dst + head);
-    // Output chunk i holds src[head + 4i .. head + 4i + 3]: the tail of source
-    // chunk i and the front of chunk i + 1 (index <= 127 since cnt <= 512).
-    switch (head) {
-    case 0:
-        for (uint32_t i = uint32_t(lane); i < body; i += 32) d4[i] = s4[i];
-        break;
-    case 1:
-        for (uint32_t i = uint32_t(lane); i < body; i += 32) {
-            const uint4 x = s4[i], y = s4[i + 1];
-            d4[i] = make_uint4(x.y, x.z, x.w, y.x);
-        }
-        break;
-    case 2:
-        for (uint32_t i = uint32_t(lane); i < body; i += 32) {
-            const uint4 x = s4[i], y = s4[i + 1];
-            d4[i] = make_uint4(x.z, x.w, y.x, y.y);
-        }
-        break;
-    default:
-        for (uint32_t i = uint32_t(lane); i < body; i += 32) {
-            const uint4 x = s4[i], y = s4[i + 1];
-            d4[i] = make_uint4(x.w, y.x, y.y, y.z);
-        }
-        break;
-    }
-    const uint32_t t0 = head + 4 * body;
-    if (uint32_t(lane) < cnt - t0) dst[t0 + lane] = src[t0 + lane];
-}
 
 }  // namespace
 

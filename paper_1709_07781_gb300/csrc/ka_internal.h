@@ -30,8 +30,8 @@ ka_status make_pred(int32_t kind, uint32_t param, PredDev *out);
     X(128, 4) X(128, 8) X(128, 16) X(256, 4) X(256, 8) X(256, 16) X(512, 4) X(512, 8) X(512, 16) X(1024, 4) X(1024, 8)
 constexpr uint32_t shape_key(uint32_t block, uint32_t ipt) { return block * 100 + ipt; }
 bool tile_supported(uint32_t block, uint32_t ipt);
-// Shapes of the warp-specialised TMA compaction kernel: (256, 16), (512, 16)
-// and (768, 16); the last exists for compaction only.
+// Shapes of the warp-specialised TMA compaction kernels (single array and
+// batch): (256, 16), (512, 16) and (768, 16); the last exists for them only.
 bool tma_shape(uint32_t block, uint32_t ipt);
 // Shape valid for `kernel` (a KA_KERNEL_* id).
 bool tile_supported_for(int32_t kernel, uint32_t block, uint32_t ipt);

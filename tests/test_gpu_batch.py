@@ -87,7 +87,10 @@ PREDS = [("lt", ki.threshold_for(0.3)), ("and_mask_eq0", 3), ("popc_odd", 0), ("
          ("ne", 0), ("all", 0)]
 
 
-@pytest.mark.parametrize("shape", [(128, 4), (256, 8), (256, 16), (512, 8)])
+TMA_SHAPES = [(768, 16), (512, 16), (256, 16)]
+
+
+@pytest.mark.parametrize("shape", [(128, 4), (256, 8), (512, 8), (128, 16)] + TMA_SHAPES)
 def test_batch_mixed_sizes_and_predicates(ka, shape):
     xs = [ki.uniform_u32(100 + i, n) for i, n in enumerate(SIZES)]
     preds = [PREDS[i % len(PREDS)] for i in range(len(xs))]
@@ -97,19 +100,46 @@ def test_batch_mixed_sizes_and_predicates(ka, shape):
     assert ws.status(ka) == 0
 
 
-def test_batch_unaligned_inputs_and_small_grid(ka):
-    xs = [ki.uniform_u32(7 + i, n) for i, n in enumerate([1000, 4097, 123, 70000, 5])]
+@pytest.mark.parametrize("shape", [None, (256, 8)] + TMA_SHAPES)
+def test_batch_unaligned_inputs_and_small_grid(ka, shape):
+    xs = [ki.uniform_u32(7 + i, n) for i, n in enumerate([1000, 4097, 123, 70000, 5, 12288, 12287, 3 * 12288 + 1])]
     preds = [("lt", ki.threshold_for(0.5))] * len(xs)
-    dst, counts, _ = run_batch(ka, xs, preds, offsets=[1, 2, 3, 0, 1], grid=3)
-    check(xs, preds, None, dst, counts)
+    for grid in (3, 0):
+        dst, counts, _ = run_batch(ka, xs, preds, offsets=[1, 2, 3, 0, 1, 2, 3, 1], grid=grid, tile=shape)
+        check(xs, preds, None, dst, counts)
 
 
-def test_batch_many_tiny_instances(ka):
-    """Thousands of one-tile items: the item search jumps far between tickets."""
+@pytest.mark.parametrize("shape", TMA_SHAPES)
+def test_batch_in_place(ka, shape):
+    """out_i == in_i for every item, inputs at every 4-byte offset."""
+    xs = [ki.uniform_u32(300 + i, n) for i, n in enumerate([70000, 3, 12289, 0, 40001, 9000])]
+    offsets = [1, 2, 3, 0, 2, 1]
+    src = Arena([x.size for x in xs], offsets=offsets)
+    host_in = src.host().copy()
+    for i, x in enumerate(xs):
+        host_in[src.offs[i]: src.offs[i] + x.size] = x
+    src.buf.copy_(torch.from_numpy(host_in.view(np.int32)))
+    counts = empty(len(xs))
+    items = np.zeros(len(xs), dtype=ITEM)
+    for i, x in enumerate(xs):
+        items[i] = (src.ptr(i), src.ptr(i), 0, counts.data_ptr() + 4 * i, x.size, ka.KA_PRED_POPC_ODD, 0, 1)
+    ws = Workspace(ka, sum(x.size for x in xs) + 1, shape, batch_items=len(xs))
+    assert ka.ka_compact_batch(table_to_dev(items), len(xs), len(xs), ws.ptr, ws.nbytes, shape, 0, stream()) == 0
+    torch.cuda.synchronize()
+    out, c = src.host(), to_host(counts, len(xs))
+    for i, x in enumerate(xs):
+        y, k = oracle.compact(oracle.map_hash(x), "popc_odd", 0)
+        assert c[i] == k and np.array_equal(out[src.offs[i]: src.offs[i] + k], y), i
+        assert np.array_equal(out[src.offs[i] + k: src.offs[i] + x.size], x[k:]), i
+
+
+@pytest.mark.parametrize("shape", [(128, 4), (768, 16)])
+def test_batch_many_tiny_instances(ka, shape):
+    """Thousands of one-tile items: the item search jumps far between tiles."""
     rng_sizes = ki.log_uniform_sizes(5, 3000, 0, 9)
     xs = [ki.uniform_u32(1000 + i, int(n)) for i, n in enumerate(rng_sizes)]
     preds = [("and_mask_eq0", 1)] * len(xs)
-    dst, counts, _ = run_batch(ka, xs, preds, tile=(128, 4))
+    dst, counts, _ = run_batch(ka, xs, preds, tile=shape)
     check(xs, preds, None, dst, counts)
 
 
@@ -123,20 +153,21 @@ def test_batch_workspace_reuse(ka):
         check(sub, preds[:len(sub)], None, dst, counts)
 
 
-def test_batch_chained_lengths_and_in_out_count(ka):
+@pytest.mark.parametrize("shape", [None, (768, 16)])
+def test_batch_chained_lengths_and_in_out_count(ka, shape):
     """Second batch reads each item's live length from the first batch's count
     words and writes its result count back into the same word."""
     xs = [ki.uniform_u32(50 + i, n) for i, n in enumerate([5000, 1, 0, 40000, 4096])]
     preds1 = [("and_mask_eq0", 1)] * 5
-    dst1, counts1, _ = run_batch(ka, xs, preds1)
+    dst1, counts1, _ = run_batch(ka, xs, preds1, tile=shape)
     counts_dev = to_dev(counts1.astype(np.uint32))
     dst2 = Arena([x.size for x in xs])
     items = np.zeros(5, dtype=ITEM)
     for i, x in enumerate(xs):
         c = counts_dev.data_ptr() + 4 * i
         items[i] = (dst1.ptr(i), dst2.ptr(i), c, c, x.size, ka.KA_PRED_MOD_NE0, 3, 0)
-    ws = Workspace(ka, sum(x.size for x in xs) + 1, None, batch_items=5)
-    assert ka.ka_compact_batch(table_to_dev(items), 5, 5, ws.ptr, ws.nbytes, None, 0, stream()) == 0
+    ws = Workspace(ka, sum(x.size for x in xs) + 1, shape, batch_items=5)
+    assert ka.ka_compact_batch(table_to_dev(items), 5, 5, ws.ptr, ws.nbytes, shape, 0, stream()) == 0
     torch.cuda.synchronize()
     out = dst2.host()
     got = to_host(counts_dev, 5)
@@ -147,7 +178,8 @@ def test_batch_chained_lengths_and_in_out_count(ka):
         assert np.array_equal(out[dst2.offs[i]: dst2.offs[i] + k2], y2)
 
 
-def test_batch_invalid_item_reports_arg_error(ka):
+@pytest.mark.parametrize("shape", [None, (768, 16)])
+def test_batch_invalid_item_reports_arg_error(ka, shape):
     xs = [ki.uniform_u32(1, 1000), ki.uniform_u32(2, 1000)]
     src = Arena([1000, 1000])
     dst = Arena([1000, 1000])
@@ -155,8 +187,8 @@ def test_batch_invalid_item_reports_arg_error(ka):
     items = np.zeros(2, dtype=ITEM)
     items[0] = (src.ptr(0), dst.ptr(0), 0, counts.data_ptr(), 1000, ka.KA_PRED_MOD_NE0, 0, 0)  # zero modulus
     items[1] = (src.ptr(1), dst.ptr(1), 0, counts.data_ptr() + 4, 1000, ka.KA_PRED_ALL, 0, 0)
-    ws = Workspace(ka, 2001, None, batch_items=2)
-    assert ka.ka_compact_batch(table_to_dev(items), 2, 2, ws.ptr, ws.nbytes, None, 0, stream()) == 0
+    ws = Workspace(ka, 2001, shape, batch_items=2)
+    assert ka.ka_compact_batch(table_to_dev(items), 2, 2, ws.ptr, ws.nbytes, shape, 0, stream()) == 0
     torch.cuda.synchronize()
     assert ws.status(ka) == ka.KA_E_ARG
     c = to_host(counts, 2)
@@ -180,7 +212,8 @@ def test_generate_batch(ka):
         assert np.all(out[o + n: o + n + 16] == SENTINEL)
 
 
-def test_batch_4096_instances_full_size(ka):
+@pytest.mark.parametrize("shape", [None, (128, 16), (768, 16)])
+def test_batch_4096_instances_full_size(ka, shape):
     """The 4096-instance workload (sizes log-uniform 2^8..2^20, per-instance
     thresholds), data generated on the device, every instance checked."""
     spec = ki.config_batch()
@@ -195,9 +228,9 @@ def test_batch_4096_instances_full_size(ka):
         gen[i] = (src.ptr(i), int(spec.seeds[i]), sizes[i], 0)
         items[i] = (src.ptr(i), dst.ptr(i), 0, counts.data_ptr() + 4 * i, sizes[i], ka.KA_PRED_LT, int(spec.t[i]), 0)
     total = sum(sizes)
-    ws = Workspace(ka, total + 1, None, batch_items=m)
+    ws = Workspace(ka, total + 1, shape, batch_items=m)
     assert ka.ka_generate_batch(table_to_dev(gen), m, m, ws.ptr, ws.nbytes, stream()) == 0
-    assert ka.ka_compact_batch(table_to_dev(items), m, m, ws.ptr, ws.nbytes, None, 0, stream()) == 0
+    assert ka.ka_compact_batch(table_to_dev(items), m, m, ws.ptr, ws.nbytes, shape, 0, stream()) == 0
     torch.cuda.synchronize()
     assert ws.status(ka) == 0
     got = to_host(counts, m)
