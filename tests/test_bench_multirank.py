@@ -1,0 +1,58 @@
+"""The benchmark's multi-rank plumbing on CPU: two gloo ranks (one process per
+GPU is the launch form; here no GPU is needed) agree on the slowest rank's
+time and on the whole-job throughput, and the reference arm runs on rank 0
+only while the other ranks exit cleanly without output."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE="2", RANK=str(rank),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import bench
+    world, r, local = bench.dist_env()
+    D = bench.Dist(world, r, local, backend="gloo")
+    D.barrier()
+    slowest = D.max(1.5 + r)  # rank 1 took longer
+    value = bench.aggregate(1000.0, world, slowest)
+    D.barrier()
+    D.close()
+    q.put((r, slowest, value))
+
+
+def test_two_gloo_ranks_agree_on_max_time_and_aggregate():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    # both ranks see the slowest rank's 2.5 s; the job processed 2 x 1000 units
+    assert got == [(0, 2.5, 800.0), (1, 2.5, 800.0)]
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    env = dict(os.environ, WORLD_SIZE="2", RANK="1", LOCAL_RANK="1", MASTER_ADDR="127.0.0.1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "3"], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == ""
