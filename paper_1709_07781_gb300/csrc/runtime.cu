@@ -215,7 +215,14 @@ struct System {
     cudaStream_t readback = nullptr;
     cudaMemPool_t pool = nullptr;
     uint64_t budget = 0;
-    std::atomic<uint64_t> in_use{0};
+    std::atomic<uint64_t> in_use{0};  // budget held: blocks handed out plus blocks in the cache
+    // Freed pool blocks kept for reuse, by size: every use of a block is
+    // ordered on `stream`, so a block freed by one request can serve the next
+    // without a cudaFreeAsync / cudaMallocFromPoolAsync pair (a few
+    // microseconds of host time each).
+    std::mutex cache_mu;
+    std::unordered_map<uint64_t, std::vector<void *>> cache;
+    uint64_t cached_bytes = 0;
     bool debug = false;
 
     // workspace for the single-pass kernels (grown on demand, stream-ordered)
@@ -242,6 +249,7 @@ struct System {
     std::mutex comp_mu;
     std::condition_variable comp_cv;
     std::deque<Completion> comp_q;
+    std::atomic<uint64_t> comp_pushed{0};  // completions queued so far (for the completer's spin)
     std::thread completer;
 
     std::atomic<int64_t> inflight{0};
@@ -259,12 +267,44 @@ constexpr uint32_t kPinnedSlots = 65536;
 
 // ---------------------------------------------------------------------------
 // References and the pool.
+constexpr uint64_t kCacheMaxBytes = 4ull << 30;
+
+// Returns every cached block to the pool (stream ordered).
+static void cache_flush(System *s) {
+    std::lock_guard<std::mutex> l(s->cache_mu);
+    for (auto &kv : s->cache)
+        for (void *p : kv.second) {
+            cudaFreeAsync(p, s->stream);
+            s->in_use.fetch_sub(kv.first);
+        }
+    s->cache.clear();
+    s->cached_bytes = 0;
+}
+
 static ka_status pool_alloc(System *s, uint64_t bytes, void **out) {
     if (bytes == 0) bytes = 256;
+    {
+        std::lock_guard<std::mutex> l(s->cache_mu);
+        auto it = s->cache.find(bytes);
+        if (it != s->cache.end() && !it->second.empty()) {
+            *out = it->second.back();
+            it->second.pop_back();
+            s->cached_bytes -= bytes;
+            return KA_OK;
+        }
+    }
     uint64_t cur = s->in_use.load();
-    do {
-        if (cur + bytes > s->budget) return KA_E_BUDGET;
-    } while (!s->in_use.compare_exchange_weak(cur, cur + bytes));
+    bool flushed = false;
+    for (;;) {
+        if (cur + bytes > s->budget) {
+            if (flushed) return KA_E_BUDGET;
+            cache_flush(s);  // cached blocks count against the budget: give them back first
+            flushed = true;
+            cur = s->in_use.load();
+            continue;
+        }
+        if (s->in_use.compare_exchange_weak(cur, cur + bytes)) break;
+    }
     cudaError_t e = cudaMallocFromPoolAsync(out, bytes, s->pool, s->stream);
     if (e != cudaSuccess) {
         s->in_use.fetch_sub(bytes);
@@ -276,8 +316,17 @@ static ka_status pool_alloc(System *s, uint64_t bytes, void **out) {
 
 static void pool_free(System *s, void *p, uint64_t bytes) {
     if (!p) return;
+    if (bytes == 0) bytes = 256;
+    {
+        std::lock_guard<std::mutex> l(s->cache_mu);
+        if (s->cached_bytes + bytes <= kCacheMaxBytes && s->cached_bytes + bytes <= s->budget / 4) {
+            s->cache[bytes].push_back(p);
+            s->cached_bytes += bytes;
+            return;
+        }
+    }
     cudaFreeAsync(p, s->stream);
-    s->in_use.fetch_sub(bytes == 0 ? 256 : bytes);
+    s->in_use.fetch_sub(bytes);
 }
 
 static ka_status new_owned_ref(System *s, uint64_t capacity, Ref **out) {
@@ -564,6 +613,7 @@ static void process(System *s, Actor *a, Msg *m) {
         std::lock_guard<std::mutex> l(s->comp_mu);
         s->comp_q.push_back({r});
     }
+    s->comp_pushed.fetch_add(1, std::memory_order_release);
     s->comp_cv.notify_one();
 }
 
@@ -586,6 +636,11 @@ static void drain_with(System *s, ka_status st) {
     }
 }
 
+// Host-side spin windows (microseconds) before a thread blocks: a blocked
+// thread costs a futex wake-up (several microseconds) when work arrives.
+constexpr int kDispatcherSpinUs = 2000;
+constexpr int kReceiveSpinUs = 2000;
+
 static void dispatcher_main(System *s) {
     cudaSetDevice(s->device);
     auto idle_since = std::chrono::steady_clock::now();
@@ -601,7 +656,9 @@ static void dispatcher_main(System *s) {
         QNode *n = s->runq.pop();
         if (!n) {
             const auto now = std::chrono::steady_clock::now();
-            if (now - idle_since < std::chrono::microseconds(200)) {
+            // stay awake for a while after the last message: a request that
+            // follows soon (the usual request/receive loop) then costs no wake-up
+            if (now - idle_since < std::chrono::microseconds(kDispatcherSpinUs)) {
                 std::this_thread::yield();
                 continue;
             }
@@ -627,9 +684,15 @@ static void dispatcher_main(System *s) {
 
 static void completer_main(System *s) {
     cudaSetDevice(s->device);
+    uint64_t taken = 0;
     for (;;) {
         Completion c;
         {
+            // spin briefly for the next completion before blocking on the queue
+            const auto t0 = std::chrono::steady_clock::now();
+            while (s->comp_pushed.load(std::memory_order_acquire) == taken && !s->stop.load() &&
+                   std::chrono::steady_clock::now() - t0 < std::chrono::microseconds(kDispatcherSpinUs))
+                std::this_thread::yield();
             std::unique_lock<std::mutex> l(s->comp_mu);
             while (s->comp_q.empty()) {
                 if (s->stop.load() && s->inflight.load() <= 0) return;
@@ -637,6 +700,7 @@ static void completer_main(System *s) {
             }
             c = s->comp_q.front();
             s->comp_q.pop_front();
+            ++taken;
         }
         Request *r = c.req;
         ka_status st = cuda_status(cudaEventSynchronize(r->event));
@@ -773,6 +837,7 @@ ka_status ka_system_destroy(ka_system *h, int32_t force) {
     s->comp_cv.notify_all();
     if (s->completer.joinable()) s->completer.join();
     cudaStreamSynchronize(s->stream);
+    cache_flush(s);
     if (s->ws) cudaFreeAsync(s->ws, s->stream);
     cudaStreamSynchronize(s->stream);
     for (cudaEvent_t e : s->events) cudaEventDestroy(e);
@@ -789,7 +854,10 @@ ka_status ka_system_destroy(ka_system *h, int32_t force) {
 ka_status ka_system_pool_bytes(ka_system *h, uint64_t *in_use, uint64_t *budget) {
     System *s = sys_of(h);
     if (!s) return KA_E_STALE;
-    if (in_use) *in_use = s->in_use.load();
+    if (in_use) {
+        std::lock_guard<std::mutex> l(s->cache_mu);
+        *in_use = s->in_use.load() - s->cached_bytes;  // bytes held by live references
+    }
     if (budget) *budget = s->budget;
     return KA_OK;
 }
@@ -1074,10 +1142,10 @@ ka_status ka_request(ka_actor *h, const ka_msg *in, ka_request_h **out) {
 ka_status ka_receive(ka_request_h *h, int64_t timeout_ns, ka_msg *out) {
     Request *r = g_requests.get(reinterpret_cast<uint64_t>(h));
     if (!r) return KA_E_STALE;
-    // brief spin (low latency), then block
+    // spin for a while (no wake-up latency for results that come soon), then block
     if (!r->done.load(std::memory_order_acquire)) {
         const auto t0 = std::chrono::steady_clock::now();
-        const auto spin = std::chrono::microseconds(100);
+        const auto spin = std::chrono::microseconds(kReceiveSpinUs);
         while (!r->done.load(std::memory_order_acquire) && std::chrono::steady_clock::now() - t0 < spin) {
         }
         if (!r->done.load(std::memory_order_acquire)) {
