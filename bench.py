@@ -308,6 +308,7 @@ def run_ours(args):
         del x, out
         torch.cuda.empty_cache()
         result["extras"]["actor_vs_direct"] = actor_overhead(ka, torch)
+        result["extras"]["microbench"] = microbench(ka, torch)
         result["extras"]["batch_4096"] = batch_large(ka, torch, peak)
         result["extras"]["serve"] = serve_large(ka, torch)
         sv = result["extras"]["serve"][0]
@@ -465,6 +466,75 @@ def actor_overhead(ka, torch):
             del x
     finally:
         ka.ka_system_destroy(sysh, 1)
+    return out
+
+
+def microbench(ka, torch):
+    """The paper's overhead experiments (Sec. 5.1, 5.2) on this library's
+    stages: wall time to spawn k actors and get one response from the last;
+    the round trip of a message through an empty-kernel actor against the
+    same empty kernel launched directly; and actor minus direct time of one
+    fused compaction across input sizes (it should not grow with N)."""
+    s, sysh = ka.ka_system_create(0)
+    ka.check(s)
+    out = {"spawn": [], "overhead_vs_n": []}
+    x = torch.empty(1 << 28, dtype=torch.int32, device="cuda")
+    ka.check(ka.ka_generate(x, 1 << 28, 9, torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    try:
+        s, ref = ka.ka_ref_wrap(sysh, x, 1024, 1024)
+        ka.check(s)
+        for k in (1, 10, 100, 1000, 10000):
+            t0 = time.perf_counter()
+            actors = []
+            for _ in range(k):
+                s, a = ka.ka_spawn_stage(sysh, ka.KA_STAGE_EMPTY)
+                ka.check(s)
+                actors.append(a)
+            s, req = ka.ka_request(actors[-1], ka.make_msg(refs=[ref]))
+            ka.check(s)
+            s, msg = ka.ka_receive(req)
+            ka.check(s)
+            dt = time.perf_counter() - t0
+            for i in range(msg.n_refs):
+                ka.ka_ref_release(msg.refs[i])
+            for a in actors:
+                ka.ka_actor_release(a)
+            out["spawn"].append({"actors": k, "seconds": round(dt, 6), "us_per_actor": round(dt / k * 1e6, 3)})
+        s, empty = ka.ka_spawn_stage(sysh, ka.KA_STAGE_EMPTY)
+        ka.check(s)
+        msg = ka.make_msg(refs=[ref])
+        ka.check(ka.ka_bench_request_loop(empty, msg, 100, 1)[0])
+        s, ta, _ = ka.ka_bench_request_loop(empty, msg, 5000, 1)
+        ka.check(s)
+        s, td, _ = ka.ka_bench_direct_chain([(ka.KA_STAGE_EMPTY, 0, 0, 0)], x, 1024, 5000)
+        ka.check(s)
+        out["empty_stage"] = {"actor_us": round(ta / 5000 * 1e6, 2), "direct_us": round(td / 5000 * 1e6, 2),
+                              "overhead_us": round((ta - td) / 5000 * 1e6, 2)}
+        ka.ka_actor_release(empty)
+        ka.ka_ref_release(ref)
+        s, comp = ka.ka_spawn_stage(sysh, ka.KA_STAGE_COMPACT, ka.KA_PRED_LT, 1 << 31)
+        ka.check(s)
+        for lg in (16, 20, 24, 28):
+            n = 1 << lg
+            iters = 2000 if lg <= 20 else (200 if lg == 24 else 50)
+            s, r = ka.ka_ref_wrap(sysh, x, n, n)
+            ka.check(s)
+            m = ka.make_msg(refs=[r])
+            ka.check(ka.ka_bench_request_loop(comp, m, 10, 1)[0])
+            s, ta, ka_ = ka.ka_bench_request_loop(comp, m, iters, 1)
+            ka.check(s)
+            s, td, kd = ka.ka_bench_direct_chain([(ka.KA_STAGE_COMPACT, ka.KA_PRED_LT, 1 << 31, 0)], x, n, iters)
+            ka.check(s)
+            ka.ka_ref_release(r)
+            out["overhead_vs_n"].append({"n": n, "actor_us": round(ta / iters * 1e6, 2),
+                                         "direct_us": round(td / iters * 1e6, 2),
+                                         "difference_us": round((ta - td) / iters * 1e6, 2),
+                                         "counts_match": int(ka_) == int(kd)})
+        ka.ka_actor_release(comp)
+    finally:
+        ka.ka_system_destroy(sysh, 1)
+    del x
     return out
 
 

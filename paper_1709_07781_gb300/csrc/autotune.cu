@@ -32,12 +32,13 @@ const ka_tile kShapes[] = {
 #undef KA_SHAPE
 };
 
-// Compaction (single array and batch) also has the TMA-only shape (768, 16).
-const ka_tile kCompactOnlyShapes[] = {{768, 16}};
+// The TMA kernels (compaction, scan, batch) also have the shape (768, 16).
+const ka_tile kTmaOnlyShapes[] = {{768, 16}};
 
 ka_tile default_tile(int32_t kernel, uint64_t n) {
     if (kernel == KA_KERNEL_COMPACT && n >= (1ull << 22)) return ka_tile{768, 16};  // TMA kernel
     if (kernel == KA_KERNEL_BATCH) return ka_tile{512, 16};                         // TMA batch kernel
+    if (kernel == KA_KERNEL_SCAN && n >= (1ull << 22)) return ka_tile{512, 16};      // TMA kernel, scan mode
     if (n >= (1ull << 24)) return ka_tile{256, 16};
     if (n >= (1ull << 21)) return ka_tile{256, 8};
     return ka_tile{256, 4};
@@ -184,7 +185,7 @@ ka_status autotune_batch(uint64_t total, const char *cache_path, ka_tile *best, 
     float win_us = 1e30f;
     if (s == KA_OK) {
         std::vector<ka_tile> shapes(std::begin(kShapes), std::end(kShapes));
-        shapes.insert(shapes.end(), std::begin(kCompactOnlyShapes), std::end(kCompactOnlyShapes));
+        shapes.insert(shapes.end(), std::begin(kTmaOnlyShapes), std::end(kTmaOnlyShapes));
         for (const ka_tile &t : shapes) {
             auto launch = [&]() -> ka_status { return ka_compact_batch(d_items, m, m, ws, ws_bytes, &t, 0, st); };
             const float us = time_launches(launch, st, 2, 9);
@@ -251,7 +252,7 @@ ka_status ka_autotune(int32_t kernel, uint64_t n, const char *cache_path, ka_til
     ka_tile win{0, 0};
     float win_us = 1e30f;
     std::vector<ka_tile> shapes(std::begin(kShapes), std::end(kShapes));
-    if (kernel == KA_KERNEL_COMPACT) shapes.insert(shapes.end(), std::begin(kCompactOnlyShapes), std::end(kCompactOnlyShapes));
+    shapes.insert(shapes.end(), std::begin(kTmaOnlyShapes), std::end(kTmaOnlyShapes));
     if (s == KA_OK) {
         for (const ka_tile &t : shapes) {
             auto launch = [&]() -> ka_status {

@@ -46,8 +46,7 @@ bool tile_supported(uint32_t block, uint32_t ipt) {
 }
 
 bool tile_supported_for(int32_t kernel, uint32_t block, uint32_t ipt) {
-    return tile_supported(block, ipt) ||
-           ((kernel == KA_KERNEL_COMPACT || kernel == KA_KERNEL_BATCH) && tma_shape(block, ipt));
+    return tile_supported(block, ipt) || tma_shape(block, ipt);  // every kernel has the TMA shapes
 }
 
 ka_status check_workspace(const void *ws, uint64_t ws_bytes, uint64_t tiles_needed) {

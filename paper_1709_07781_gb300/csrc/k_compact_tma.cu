@@ -1,5 +1,9 @@
-// Fused single-pass compaction: a persistent, warp-specialised kernel fed by
-// TMA bulk copies, whose compute warps never wait for one another.
+// Fused single-pass compaction, and single-pass exclusive scan, as one
+// persistent, warp-specialised kernel fed by TMA bulk copies, whose compute
+// warps never wait for one another. The scan (k_scan_tma) differs only in
+// what a compute warp does with its segment: it scans it in place and later
+// writes every entry plus the segment's offset (below, "count" and "kept"
+// read "sum").
 //
 // Layout of the work. The grid holds exactly the blocks that fit on the GPU at
 // once (cooperative launch), G of them; block b owns tiles b, b + G, b + 2G, ...
@@ -51,16 +55,21 @@ struct TmaArgs {
     uint32_t n;
     uint32_t status_cap;
     uint32_t mul;
-    uint32_t lead;  // 0..3 entries before the input's first entry
+    uint32_t lead;     // 0..3 entries before the input's first entry
+    uint32_t out_vec;  // scan: out - lead is 16-byte aligned (output entries align with input entries)
     PredDev pred;
 };
 
 }  // namespace
 
-// CWW compute warps (tile = CWW * 512 entries), S stages, write-out LAG tiles
-// after counting, at most MAXG blocks, MINB blocks per SM.
-template <int CWW, int S, int LAG, int MAXG, int MINB>
-__global__ void __launch_bounds__((CWW + 2) * 32, MINB) k_compact_tma(const TmaArgs a) {
+// One pass of the warp-specialised kernel. SCAN = false: fused compaction
+// (count, compact in place, write out the kept entries). SCAN = true:
+// exclusive prefix sum (scan each segment in place, write every entry plus
+// its offset; a.count receives the total). CWW compute warps (tile = CWW *
+// 512 entries), S stages, write-out LAG tiles after counting, at most MAXG
+// blocks.
+template <bool SCAN, int CWW, int S, int LAG, int MAXG>
+__device__ __forceinline__ void tma_pass(const TmaArgs &a) {
     constexpr int T = CWW * kSeg, ROWS = 4;
     constexpr int K = (MAXG + 31) / 32;
     static_assert(LAG >= 1 && LAG < S && LAG <= 3, "a stage is written out before its refill; slots repeat every 4");
@@ -224,7 +233,34 @@ __global__ void __launch_bounds__((CWW + 2) * 32, MINB) k_compact_tma(const TmaA
             const uint32_t cnt = s_wcnt[k][w];
             const uint32_t off = s_woff[k][w];
             __syncwarp();
-            if (ok && s_err[k] == 0u && cnt != 0u) warp_copy_out(seg_base + size_t(s) * T, a.out + off, cnt, lane);
+            if constexpr (!SCAN) {
+                if (ok && s_err[k] == 0u && cnt != 0u)
+                    warp_copy_out(seg_base + size_t(s) * T, a.out + off, cnt, lane);
+            } else if (ok && s_err[k] == 0u) {
+                // every input entry of the segment, plus the segment's offset, at its own index
+                const uint32_t base = (b + jp * G) * uint32_t(T) + uint32_t(w) * kSeg;
+                const uint32_t vlo = base < a.lead ? a.lead - base : 0u;
+                const uint32_t vhi = n > base ? min(n - base, uint32_t(kSeg)) : 0u;
+                const uint32_t *sg = seg_base + size_t(s) * T;
+                uint32_t *dst = a.out - a.lead + base;  // entry i of the output is a.out[i]
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    const uint32_t e0 = uint32_t(r * 128 + lane * 4);
+                    uint4 q = *reinterpret_cast<const uint4 *>(sg + e0);
+                    q.x += off;
+                    q.y += off;
+                    q.z += off;
+                    q.w += off;
+                    if (a.out_vec && e0 >= vlo && e0 + 4 <= vhi) {
+                        *reinterpret_cast<uint4 *>(dst + e0) = q;
+                    } else {
+                        if (e0 >= vlo && e0 < vhi) dst[e0] = q.x;
+                        if (e0 + 1 >= vlo && e0 + 1 < vhi) dst[e0 + 1] = q.y;
+                        if (e0 + 2 >= vlo && e0 + 2 < vhi) dst[e0 + 2] = q.z;
+                        if (e0 + 3 >= vlo && e0 + 3 < vhi) dst[e0 + 3] = q.w;
+                    }
+                }
+            }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty_bar[s]);  // this warp is done with the stage
         }
@@ -245,57 +281,107 @@ __global__ void __launch_bounds__((CWW + 2) * 32, MINB) k_compact_tma(const TmaA
                     seg[e] = e >= vlo && e < vhi ? src[e] : 0u;
                 __syncwarp();
             }
-            uint32_t v[ROWS][4], m[ROWS], packed = 0;
+            uint32_t rowbase = 0;  // kept entries (compaction) or sum (scan) of this segment
+            if constexpr (SCAN) {
+                uint32_t v[ROWS][4];
 #pragma unroll
-            for (int r = 0; r < ROWS; ++r) {
-                const uint32_t e0 = uint32_t(r * 128 + lane * 4);
-                const uint4 q = *reinterpret_cast<const uint4 *>(seg + e0);
-                v[r][0] = q.x;
-                v[r][1] = q.y;
-                v[r][2] = q.z;
-                v[r][3] = q.w;
-            }
-            if (mul != 1u) {
+                for (int r = 0; r < ROWS; ++r) {
+                    const uint32_t e0 = uint32_t(r * 128 + lane * 4);
+                    const uint4 q = *reinterpret_cast<const uint4 *>(seg + e0);
+                    v[r][0] = q.x;
+                    v[r][1] = q.y;
+                    v[r][2] = q.z;
+                    v[r][3] = q.w;
+                    if (vlo != 0u || vhi != uint32_t(kSeg)) {
 #pragma unroll
-                for (int r = 0; r < ROWS; ++r)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) v[r][c] *= mul;
-            }
-#pragma unroll
-            for (int r = 0; r < ROWS; ++r) {
-                const uint32_t e0 = uint32_t(r * 128 + lane * 4);
-                uint32_t mk = pred_mask4(a.pred, v[r][0], v[r][1], v[r][2], v[r][3]);
-                if (vlo != 0u || vhi != uint32_t(kSeg)) {
-                    const uint32_t skip = vlo > e0 ? min(vlo - e0, 4u) : 0u;
-                    const uint32_t left = vhi > e0 ? vhi - e0 : 0u;
-                    mk &= (0xFu << skip) & (left >= 4 ? 0xFu : ((1u << left) - 1u));
+                        for (int c = 0; c < 4; ++c)
+                            if (e0 + c < vlo || e0 + c >= vhi) v[r][c] = 0u;
+                    }
                 }
-                m[r] = mk;
-                packed += uint32_t(__popc(mk)) << (8 * r);
-            }
-            // per-row counts, 8 bits each (a row of the warp keeps at most 128)
-            const uint32_t incl = warp_incl_scan(packed, lane);
-            const uint32_t excl = incl - packed;
-            const uint32_t rows = __shfl_sync(kFull, incl, 31);
-            __syncwarp();  // every lane holds its entries before any is overwritten
-            uint32_t rowbase = 0;
+                uint32_t rs[ROWS], incl[ROWS];
 #pragma unroll
-            for (int r = 0; r < ROWS; ++r) {
-                uint32_t pos = rowbase + ((excl >> (8 * r)) & 0xFFu);
+                for (int r = 0; r < ROWS; ++r) rs[r] = v[r][0] + v[r][1] + v[r][2] + v[r][3];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    if ((m[r] >> c) & 1u) seg[pos++] = v[r][c];
+                for (int r = 0; r < ROWS; ++r) incl[r] = warp_incl_scan(rs[r], lane);
+                // in place: every lane rewrites only the entries it read
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    const uint32_t e0 = uint32_t(r * 128 + lane * 4);
+                    uint32_t x = rowbase + incl[r] - rs[r];
+                    uint4 o;
+                    o.x = x;
+                    x += v[r][0];
+                    o.y = x;
+                    x += v[r][1];
+                    o.z = x;
+                    x += v[r][2];
+                    o.w = x;
+                    *reinterpret_cast<uint4 *>(seg + e0) = o;
+                    rowbase += __shfl_sync(kFull, incl[r], 31);
                 }
-                rowbase += (rows >> (8 * r)) & 0xFFu;
+            } else {
+                uint32_t v[ROWS][4], m[ROWS], packed = 0;
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    const uint32_t e0 = uint32_t(r * 128 + lane * 4);
+                    const uint4 q = *reinterpret_cast<const uint4 *>(seg + e0);
+                    v[r][0] = q.x;
+                    v[r][1] = q.y;
+                    v[r][2] = q.z;
+                    v[r][3] = q.w;
+                }
+                if (mul != 1u) {
+#pragma unroll
+                    for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) v[r][c] *= mul;
+                }
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    const uint32_t e0 = uint32_t(r * 128 + lane * 4);
+                    uint32_t mk = pred_mask4(a.pred, v[r][0], v[r][1], v[r][2], v[r][3]);
+                    if (vlo != 0u || vhi != uint32_t(kSeg)) {
+                        const uint32_t skip = vlo > e0 ? min(vlo - e0, 4u) : 0u;
+                        const uint32_t left = vhi > e0 ? vhi - e0 : 0u;
+                        mk &= (0xFu << skip) & (left >= 4 ? 0xFu : ((1u << left) - 1u));
+                    }
+                    m[r] = mk;
+                    packed += uint32_t(__popc(mk)) << (8 * r);
+                }
+                // per-row counts, 8 bits each (a row of the warp keeps at most 128)
+                const uint32_t incl = warp_incl_scan(packed, lane);
+                const uint32_t excl = incl - packed;
+                const uint32_t rows = __shfl_sync(kFull, incl, 31);
+                __syncwarp();  // every lane holds its entries before any is overwritten
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    uint32_t pos = rowbase + ((excl >> (8 * r)) & 0xFFu);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        if ((m[r] >> c) & 1u) seg[pos++] = v[r][c];
+                    }
+                    rowbase += (rows >> (8 * r)) & 0xFFu;
+                }
             }
             if (lane == 0) {
                 s_wcnt[k][w] = rowbase;
                 // the last segment counted publishes the tile aggregate at once
-                const uint32_t prev = atomicAdd(&s_pack[k], (1u << 16) | rowbase);
-                if ((prev >> 16) == uint32_t(CWW - 1)) {
-                    s_pack[k] = 0;
-                    st_relaxed_u64(status_at(agg_words, tile),
-                                   pack_status(epoch, kFlagAggregate, (prev & 0xFFFFu) + rowbase));
+                if constexpr (!SCAN) {
+                    const uint32_t prev = atomicAdd(&s_pack[k], (1u << 16) | rowbase);
+                    if ((prev >> 16) == uint32_t(CWW - 1)) {
+                        s_pack[k] = 0;
+                        st_relaxed_u64(status_at(agg_words, tile),
+                                       pack_status(epoch, kFlagAggregate, (prev & 0xFFFFu) + rowbase));
+                    }
+                } else {  // segment sums are full 32-bit values: the last warp adds them up
+                    __threadfence_block();
+                    if (atomicAdd(&s_pack[k], 1u) == uint32_t(CWW - 1)) {
+                        __threadfence_block();
+                        uint32_t agg = 0;
+                        for (int q = 0; q < CWW; ++q) agg += s_wcnt[k][q];
+                        s_pack[k] = 0;
+                        st_relaxed_u64(status_at(agg_words, tile), pack_status(epoch, kFlagAggregate, agg));
+                    }
                 }
             }
             __syncwarp();
@@ -304,13 +390,23 @@ __global__ void __launch_bounds__((CWW + 2) * 32, MINB) k_compact_tma(const TmaA
     }
 }
 
-namespace {
+template <int CWW, int S, int LAG, int MAXG, int MINB>
+__global__ void __launch_bounds__((CWW + 2) * 32, MINB) k_compact_tma(const TmaArgs a) {
+    tma_pass<false, CWW, S, LAG, MAXG>(a);
+}
 
 template <int CWW, int S, int LAG, int MAXG, int MINB>
+__global__ void __launch_bounds__((CWW + 2) * 32, MINB) k_scan_tma(const TmaArgs a) {
+    tma_pass<true, CWW, S, LAG, MAXG>(a);
+}
+
+namespace {
+
+template <bool SCAN, int CWW, int S, int LAG, int MAXG, int MINB>
 ka_status launch_tma_shape(const TmaArgs &a, uint64_t cap, cudaStream_t stream) {
     constexpr int BLOCK = (CWW + 2) * 32, T = CWW * kSeg;
     const size_t smem = size_t(S) * T * 4;
-    auto kern = k_compact_tma<CWW, S, LAG, MAXG, MINB>;
+    auto kern = SCAN ? k_scan_tma<CWW, S, LAG, MAXG, MINB> : k_compact_tma<CWW, S, LAG, MAXG, MINB>;
     static int grid_cached = 0;
     if (grid_cached == 0) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
@@ -337,6 +433,16 @@ ka_status launch_tma_shape(const TmaArgs &a, uint64_t cap, cudaStream_t stream) 
     return cuda_status(cudaLaunchKernelEx(&cfg, kern, a));
 }
 
+// tile (768, 16): 24 compute warps, 12288 entries, 4 stages of 48 KiB, 1 block per SM;
+// tile (512, 16): 16 compute warps, 8192 entries, 3 stages of 32 KiB, 2 blocks per SM;
+// tile (256, 16): 8 compute warps, 4096 entries, 4 stages of 16 KiB, 3 blocks per SM.
+template <bool SCAN>
+ka_status launch_tma(const TmaArgs &a, ka_tile tile, uint64_t cap, cudaStream_t stream) {
+    if (tile.block == 768) return launch_tma_shape<SCAN, 24, 4, 3, 160, 1>(a, cap, stream);
+    if (tile.block == 512) return launch_tma_shape<SCAN, 16, 3, 2, 320, 2>(a, cap, stream);
+    return launch_tma_shape<SCAN, 8, 4, 2, 480, 3>(a, cap, stream);
+}
+
 }  // namespace
 
 bool tma_shape(uint32_t block, uint32_t ipt) {
@@ -361,12 +467,26 @@ ka_status launch_compact_tma(const CompactLaunch &L, cudaStream_t stream) {
     a.status_cap = status_capacity(L.ws_bytes);
     a.mul = L.mul;
     a.pred = L.pred;
-    // tile (768, 16): 24 compute warps, 12288 entries, 4 stages of 48 KiB, 1 block per SM;
-    // tile (512, 16): 16 compute warps, 8192 entries, 3 stages of 32 KiB, 2 blocks per SM;
-    // tile (256, 16): 8 compute warps, 4096 entries, 4 stages of 16 KiB, 3 blocks per SM.
-    if (L.tile.block == 768) return launch_tma_shape<24, 4, 3, 160, 1>(a, L.n + a.lead, stream);
-    if (L.tile.block == 512) return launch_tma_shape<16, 3, 2, 320, 2>(a, L.n + a.lead, stream);
-    return launch_tma_shape<8, 4, 2, 480, 3>(a, L.n + a.lead, stream);
+    a.out_vec = 0;
+    return launch_tma<false>(a, L.tile, L.n + a.lead, stream);
+}
+
+ka_status launch_scan_tma(const uint32_t *in, uint64_t n, const uint32_t *n_ptr, uint32_t *out, uint32_t *total,
+                          void *ws, uint64_t ws_bytes, ka_tile tile, cudaStream_t stream) {
+    TmaArgs a;
+    a.lead = uint32_t(reinterpret_cast<uintptr_t>(in) & 15u) / 4u;
+    a.in = in - a.lead;
+    a.out = out;
+    a.out_vec = ((reinterpret_cast<uintptr_t>(out) - 4u * a.lead) & 15u) == 0 ? 1u : 0u;
+    a.n_ptr = n_ptr;
+    a.count = total;
+    a.ws = static_cast<WsHeader *>(ws);
+    a.status = reinterpret_cast<uint64_t *>(static_cast<char *>(ws) + kWsHeaderBytes);
+    a.n = uint32_t(n);
+    a.status_cap = status_capacity(ws_bytes);
+    a.mul = 1u;
+    a.pred = PredDev{};
+    return launch_tma<true>(a, tile, n + a.lead, stream);
 }
 
 }  // namespace ka

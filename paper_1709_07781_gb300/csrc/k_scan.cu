@@ -168,9 +168,12 @@ ka_status launch_exclusive_scan(const uint32_t *in, uint64_t n, const uint32_t *
                                 uint32_t *total, void *ws, uint64_t ws_bytes, ka_tile t, cudaStream_t stream) {
     if (n > 0xFFFFFFFFull || (n && (!in || !out)) || !total) return KA_E_ARG;
     if (n_ptr && n_ptr == total) return KA_E_ARG;
-    if (!tile_supported(t.block, t.ipt)) return KA_E_ARG;
+    if (!tile_supported_for(KA_KERNEL_SCAN, t.block, t.ipt)) return KA_E_ARG;
     const ka_status ws_ok = check_workspace(ws, ws_bytes, tiles_for(n, t.block * t.ipt));
     if (ws_ok != KA_OK) return ws_ok;
+    if (tma_shape(t.block, t.ipt) && n <= 0xFFFFFFFCull)
+        return launch_scan_tma(in, n, n_ptr, out, total, ws, ws_bytes, t, stream);
+    if (!tile_supported(t.block, t.ipt)) return KA_E_ARG;  // a TMA-only shape beyond its size limit
     ScanArgs a;
     a.in = in;
     a.out = out;

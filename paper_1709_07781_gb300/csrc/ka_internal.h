@@ -30,8 +30,8 @@ ka_status make_pred(int32_t kind, uint32_t param, PredDev *out);
     X(128, 4) X(128, 8) X(128, 16) X(256, 4) X(256, 8) X(256, 16) X(512, 4) X(512, 8) X(512, 16) X(1024, 4) X(1024, 8)
 constexpr uint32_t shape_key(uint32_t block, uint32_t ipt) { return block * 100 + ipt; }
 bool tile_supported(uint32_t block, uint32_t ipt);
-// Shapes of the warp-specialised TMA compaction kernels (single array and
-// batch): (256, 16), (512, 16) and (768, 16); the last exists for them only.
+// Shapes of the warp-specialised TMA kernels (compaction, scan, batch):
+// (256, 16), (512, 16) and (768, 16); the last exists for them only.
 bool tma_shape(uint32_t block, uint32_t ipt);
 // Shape valid for `kernel` (a KA_KERNEL_* id).
 bool tile_supported_for(int32_t kernel, uint32_t block, uint32_t ipt);
@@ -77,6 +77,9 @@ ka_status launch_compact(const CompactLaunch &L, cudaStream_t stream);
 bool compact_tma_eligible(const CompactLaunch &L);
 ka_status launch_compact_tma(const CompactLaunch &L, cudaStream_t stream);
 
+// The warp-specialised TMA kernel in scan mode (TMA shapes).
+ka_status launch_scan_tma(const uint32_t *in, uint64_t n, const uint32_t *n_ptr, uint32_t *out, uint32_t *total,
+                          void *ws, uint64_t ws_bytes, ka_tile tile, cudaStream_t stream);
 ka_status launch_exclusive_scan(const uint32_t *in, uint64_t n, const uint32_t *n_ptr, uint32_t *out,
                                 uint32_t *total, void *ws, uint64_t ws_bytes, ka_tile tile,
                                 cudaStream_t stream);

@@ -17,7 +17,8 @@ from gpu_util import SENTINEL, Workspace, empty, stream, to_dev, to_host, word  
 
 SHAPES = [(128, 4), (128, 8), (128, 16), (256, 4), (256, 8), (256, 16), (512, 4), (512, 8)]
 SIZES = [0, 1, 3, 4, 5, 127, 511, 512, 513, 1023, 1025, 2047, 2048, 2049, 4095, 4096, 4097, 3 * 4096 + 17,
-         65537, (1 << 20) + 3]
+         12287, 12288, 12289, 65537, (1 << 20) + 3]
+TMA_SHAPES = [(768, 16), (512, 16)]  # (256, 16) is in SHAPES
 PREDS = [("and_mask_eq0", 3), ("lt", ki.threshold_for(0.5)), ("topbits_lt", 8), ("popc_odd", 0),
          ("mod_ne0", 3), ("ne", 0), ("mod_ne0", 12), ("topbits_lt", 0), ("lt", 0), ("lt", 0xFFFFFFFF)]
 
@@ -96,7 +97,7 @@ def test_predicate_rejects_zero_modulus(ka):
 
 
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("shape", SHAPES + TMA_SHAPES)
 def test_exclusive_scan_shapes_and_sizes(ka, shape):
     ws = Workspace(ka, (1 << 20) + 64, shape)
     for n in SIZES:
@@ -117,22 +118,58 @@ def test_exclusive_scan_shapes_and_sizes(ka, shape):
     assert ws.status(ka) == 0
 
 
-def test_exclusive_scan_in_place_and_unaligned(ka):
+@pytest.mark.parametrize("shape", [None, (768, 16), (512, 16), (256, 16)])
+def test_exclusive_scan_in_place_and_unaligned(ka, shape):
     n = 100003
     v = ki.uniform_u32(5, n)
     o, tot = oracle.exclusive_scan(v)
     ws = Workspace(ka, n + 8)
     d = to_dev(v)
     total = empty(1)
-    assert ka.ka_exclusive_scan(d, n, None, d, total, ws.ptr, ws.nbytes, None, stream()) == 0
+    assert ka.ka_exclusive_scan(d, n, None, d, total, ws.ptr, ws.nbytes, shape, stream()) == 0
     torch.cuda.synchronize()
     assert np.array_equal(to_host(d, n), o) and word(total) == tot
-    for off in (1, 2, 3):
-        d = to_dev(np.concatenate([np.zeros(off, np.uint32), v]))
-        out = empty(n + off)
-        assert ka.ka_exclusive_scan(d[off:], n, None, out[off:], total, ws.ptr, ws.nbytes, None, stream()) == 0
+    # input and output views at every 4-byte offset, matching and not
+    for off_in, off_out in ((1, 1), (2, 2), (3, 3), (1, 0), (0, 3), (2, 1)):
+        d = to_dev(np.concatenate([np.zeros(off_in, np.uint32), v]))
+        out = empty(n + off_out + 4)
+        assert ka.ka_exclusive_scan(d[off_in:], n, None, out[off_out:], total, ws.ptr, ws.nbytes, shape,
+                                    stream()) == 0
         torch.cuda.synchronize()
-        assert np.array_equal(to_host(out[off:], n), o) and word(total) == tot
+        got = to_host(out)
+        assert np.array_equal(got[off_out:off_out + n], o) and word(total) == tot, (off_in, off_out)
+        assert np.all(got[:off_out] == SENTINEL) and np.all(got[off_out + n:] == SENTINEL)
+
+
+@pytest.mark.parametrize("shape", TMA_SHAPES)
+def test_exclusive_scan_live_length_and_full_size(ka, shape):
+    """Live length from a device word; the N = 2^28 flags of the three-launch
+    comparison (keep x < 2^31), every output checked."""
+    n = (1 << 22) + 9
+    v = (ki.uniform_u32(6, n) & 1).astype(np.uint32)
+    live = n - 12345
+    d_n = to_dev(np.array([live], dtype=np.uint32))
+    ws = Workspace(ka, n, shape)
+    out, total = empty(n), empty(1)
+    assert ka.ka_exclusive_scan(to_dev(v), n, d_n, out, total, ws.ptr, ws.nbytes, shape, stream()) == 0
+    torch.cuda.synchronize()
+    o, tot = oracle.exclusive_scan(v[:live])
+    got = to_host(out)
+    assert np.array_equal(got[:live], o) and word(total) == tot and np.all(got[live:] == SENTINEL)
+    N = 1 << 28
+    x = torch.empty(N, dtype=torch.int32, device="cuda")
+    assert ka.ka_generate(x, N, 2, stream()) == 0
+    f = torch.empty_like(x)
+    assert ka.ka_predicate(x, N, None, ka.KA_PRED_LT, 1 << 31, f, stream()) == 0
+    del x
+    ws = Workspace(ka, N, shape)
+    o_dev, total = torch.empty_like(f), empty(1)
+    assert ka.ka_exclusive_scan(f, N, None, o_dev, total, ws.ptr, ws.nbytes, shape, stream()) == 0
+    torch.cuda.synchronize()
+    flags = to_host(f)
+    del f
+    o, tot = oracle.exclusive_scan(flags)
+    assert word(total) == tot and np.array_equal(to_host(o_dev), o)
 
 
 # ---------------------------------------------------------------------------
