@@ -399,13 +399,35 @@ def three_launch_large(ka, torch, x, thresholds, D, peak):
                 times["exclusive_scan"] += e[1].elapsed_time(e[2]) / reps
                 times["scatter"] += e[2].elapsed_time(e[3]) / reps
         k = int(total[0].item()) & 0xFFFFFFFF
+        # the three-phase tile method on the same input: 8N + 4K bytes
+        s, tpb = ka.ka_three_phase_workspace_size(N)
+        ka.check(s)
+        tp_t = torch.empty(tpb + 256, dtype=torch.uint8, device=x.device)
+        tp = (tp_t.data_ptr() + 255) // 256 * 256
+        ka.check(ka.ka_workspace_init(tp, tpb, st.cuda_stream))
+        tp_us = 0.0
+        for r in range(reps + 2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            ka.check(ka.ka_compact_three_phase(x, N, None, ka.KA_PRED_LT, t, 0, y, total[1:2], tp, tpb,
+                                               st.cuda_stream))
+            e1.record(st)
+            torch.cuda.synchronize()
+            if r >= 2:
+                tp_us += e0.elapsed_time(e1) * 1000.0 / reps
+        del tp_t
+        k_tp = int(total[1].item()) & 0xFFFFFFFF
+        tp_bytes = 8.0 * N + 4.0 * k_tp
         bytes_ = {"predicate": 8.0 * N, "exclusive_scan": 8.0 * N, "scatter": 12.0 * N + 4.0 * k}
         ms = sum(times.values())
         out.append({"s": SELECTIVITIES[i], "ms": round(ms, 4), "elements/s": N / (ms / 1000),
                     "kernels": {kname: {"us": round(tv * 1000, 2),
                                         "GB/s": round(bytes_[kname] / (tv / 1000) / 1e9, 1),
                                         "frac": round(bytes_[kname] / (tv / 1000) / 1e9 / peak, 4)}
-                                for kname, tv in times.items()}})
+                                for kname, tv in times.items()},
+                    "three_phase": {"us": round(tp_us, 2), "GB/s": round(tp_bytes / (tp_us * 1e-6) / 1e9, 1),
+                                    "frac": round(tp_bytes / (tp_us * 1e-6) / 1e9 / peak, 4),
+                                    "elements/s": N / (tp_us * 1e-6), "counts_match": k_tp == k}})
     return out
 
 

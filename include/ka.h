@@ -187,6 +187,17 @@ ka_status ka_compact_static(const uint32_t *d_in, uint64_t n, const uint32_t *d_
                             uint32_t param, uint32_t xform, uint32_t *d_out, uint32_t *d_count,
                             const ka_tile *tile, void *stream);
 
+/* Three-phase compaction (Sec. 4.1: count, prefix sum, move, after Billeter
+ * et al.): per-tile kept counts (tiles of 4096 entries), an exclusive scan
+ * of the counts, then each kept entry moved to its tile's offset plus its rank
+ * in the tile. Same result as ka_compact; reads the input twice. Workspace:
+ * ka_three_phase_workspace_size bytes, 256-byte aligned, initialised once
+ * with ka_workspace_init. d_count must not alias d_n. */
+ka_status ka_three_phase_workspace_size(uint64_t capacity, uint64_t *bytes);
+ka_status ka_compact_three_phase(const uint32_t *d_in, uint64_t n, const uint32_t *d_n, int32_t pred,
+                                 uint32_t param, uint32_t xform, uint32_t *d_out, uint32_t *d_count,
+                                 void *d_ws, uint64_t ws_bytes, void *stream);
+
 /* Interleave of fuseFillsLiterals (Sec. 4.1, Listing 5): d_index[2i] =
  * d_chunk_ids[i], d_index[2i+1] = d_literals[i] for i < live k; d_n_out
  * (optional) receives 2 * live k. */

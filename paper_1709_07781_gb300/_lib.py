@@ -127,6 +127,9 @@ _SIGS = {
                                     c_vp, c_vp, c_vp, ctypes.c_uint64, ctypes.POINTER(ka_tile), c_vp]),
     "ka_compact_static": (ctypes.c_int32, [c_vp, ctypes.c_uint64, c_vp, ctypes.c_int32, ctypes.c_uint32,
                                            ctypes.c_uint32, c_vp, c_vp, ctypes.POINTER(ka_tile), c_vp]),
+    "ka_three_phase_workspace_size": (ctypes.c_int32, [ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
+    "ka_compact_three_phase": (ctypes.c_int32, [c_vp, ctypes.c_uint64, c_vp, ctypes.c_int32, ctypes.c_uint32,
+                                                ctypes.c_uint32, c_vp, c_vp, c_vp, ctypes.c_uint64, c_vp]),
     "ka_prepare_index": (ctypes.c_int32, [c_vp, c_vp, ctypes.c_uint64, c_vp, c_vp, c_vp, c_vp]),
     "ka_batch_workspace_size": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(ka_tile),
                                                  ctypes.POINTER(ctypes.c_uint64)]),
@@ -275,6 +278,18 @@ def ka_compact_static(d_in, n: int, d_n, pred: int, param: int, xform: int, d_ou
                       stream=None) -> int:
     return lib.ka_compact_static(ptr(d_in), n, ptr(d_n), pred, param, xform, ptr(d_out), ptr(d_count),
                                  _tile(tile), stream_ptr(stream))
+
+
+def ka_three_phase_workspace_size(capacity: int):
+    out = ctypes.c_uint64(0)
+    s = lib.ka_three_phase_workspace_size(capacity, ctypes.byref(out))
+    return s, out.value
+
+
+def ka_compact_three_phase(d_in, n: int, d_n, pred: int, param: int, xform: int, d_out, d_count, d_ws,
+                           ws_bytes: int, stream=None) -> int:
+    return lib.ka_compact_three_phase(ptr(d_in), n, ptr(d_n), pred, param, xform, ptr(d_out), ptr(d_count),
+                                      ptr(d_ws), ws_bytes, stream_ptr(stream))
 
 
 def ka_prepare_index(d_chunk_ids, d_literals, k: int, d_k, d_index, d_n_out=None, stream=None) -> int:

@@ -391,3 +391,47 @@ def test_pipeline4_direct(ka, fused):
         assert k == expect[i].size
         assert np.array_equal(to_host(bufs[i], k), expect[i])
         assert np.all(to_host(bufs[i])[k:n + 8] == SENTINEL)
+
+
+# ---------------------------------------------------------------------------
+def three_phase(ka, d_x, n, pred, param, xform=0, d_n=None, ws=None, cap=None):
+    cap = n if cap is None else cap
+    if ws is None:
+        s, nb = ka.ka_three_phase_workspace_size(cap)
+        assert s == 0
+        buf = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+        ptr = (buf.data_ptr() + 255) // 256 * 256
+        assert ka.ka_workspace_init(ptr, nb, stream()) == 0
+        ws = (buf, ptr, nb)
+    out, count = empty(cap + 16), empty(1)
+    s = ka.ka_compact_three_phase(d_x, cap if d_n is not None else n, d_n, ka.PRED[pred], param, xform, out, count,
+                                  ws[1], ws[2], stream())
+    assert s == 0, ka.ka_strerror(s)
+    torch.cuda.synchronize()
+    return out, word(count), ws
+
+
+@pytest.mark.parametrize("pred,param", PREDS[:6])
+def test_three_phase_billeter(ka, pred, param):
+    """Count per tile, scan of the counts, move: the same result as the oracle
+    (sizes across tile boundaries, hash transform, unaligned input)."""
+    for n in [0, 1, 4095, 4096, 4097, 3 * 4096 + 5, 100003, (1 << 20) + 7]:
+        x = ki.uniform_u32(n + 3, n + 3)
+        for xform in (0, 1):
+            for off in (0, 1):
+                out, k, _ = three_phase(ka, to_dev(x)[off:], n, pred, param, xform)
+                src = x[off:off + n]
+                y, ek = oracle.compact(oracle.map_hash(src) if xform else src, pred, param)
+                assert k == ek and np.array_equal(to_host(out, k), y), (n, xform, off)
+                assert np.all(to_host(out)[k:n + 16] == SENTINEL)
+
+
+def test_three_phase_live_length_and_reuse(ka):
+    n = (1 << 21) + 11
+    x = ki.uniform_u32(42, n)
+    ws = None
+    for rep, live in enumerate([n, 5, 0, 12345, n - 1, 4096]):
+        d_n = to_dev(np.array([live], dtype=np.uint32))
+        out, k, ws = three_phase(ka, to_dev(x), n, "lt", ki.threshold_for(0.3), d_n=d_n, ws=ws)
+        y, ek = oracle.compact(x[:live], "lt", ki.threshold_for(0.3))
+        assert k == ek and np.array_equal(to_host(out, k), y), rep
