@@ -39,7 +39,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC])
         os.replace(tmp, _SO)
     return _SO
 
@@ -65,6 +65,9 @@ def bind(L):
     L.ora_map_hash.argtypes = [u32p, ctypes.c_uint64, u32p]
     L.ora_prepare_index.restype = None
     L.ora_prepare_index.argtypes = [u32p, u32p, ctypes.c_uint64, u32p]
+    L.ora_mandelbrot.restype = None
+    L.ora_mandelbrot.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                 ctypes.c_float, ctypes.c_uint32, u32p]
     return L
 
 
@@ -171,6 +174,19 @@ def prepare_index(chunk_ids, literals) -> np.ndarray:
 # ----------------------------------------------------------------------------
 # Compositions (Sec. 3.5: C = B o A feeds A's result, with its length, to B).
 # ----------------------------------------------------------------------------
+
+def mandelbrot(width: int, height: int, re_min: float, im_min: float, re_max: float, im_max: float,
+               max_iter: int) -> np.ndarray:
+    """Escape-time image (Sec. 5.4), uint32 [height, width], row 0 at im_min."""
+    out = np.zeros(width * height, dtype=np.uint32)
+    lib().ora_mandelbrot(width, height, re_min, im_min, re_max, im_max, max_iter, _p(out))
+    return out.reshape(height, width)
+
+
+# The rectangle of the paper's Mandelbrot workload (Sec. 5.4): from
+# -0.5 - 0.7375i to 0.1 - 0.1375i.
+MANDELBROT_REGION = (-0.5, -0.7375, 0.1, -0.1375)
+
 
 def three_phase(x, pred: str, param: int):
     """Flag, exclusive scan, move (Sec. 4.1). Returns (f, o, total, y)."""

@@ -145,3 +145,41 @@ void ora_prepare_index(const uint32_t *chunk_ids, const uint32_t *literals, uint
         index[2 * i + 1] = literals[i];
     }
 }
+
+/*
+ * Escape-time Mandelbrot image (the paper's compute workload, Sec. 5.4):
+ * pixel (x, y) of a width x height image over the rectangle with lower-left
+ * corner (re_min, im_min) is the point c = (re_min + x dre, im_min + y dim),
+ * dre = (re_max - re_min) / width, dim = (im_max - im_min) / height. Starting
+ * from z = 0, z <- z^2 + c is applied while |z|^2 <= 4, at most max_iter
+ * times; the pixel's value is the number of steps taken. Every operation is
+ * one IEEE single-precision operation in the order written (this file is
+ * built without floating-point contraction), so the result is exact and
+ * reproducible: z^2 + c is (zr zr - zi zi + cr, (2 zr) zi + ci) and |z|^2 is
+ * zr zr + zi zi. Row y = 0 is the bottom row of the rectangle; out is row-major.
+ */
+void ora_mandelbrot(uint32_t width, uint32_t height, float re_min, float im_min, float re_max, float im_max,
+                    uint32_t max_iter, uint32_t *out)
+{
+    const float dre = (re_max - re_min) / (float)width;
+    const float dim = (im_max - im_min) / (float)height;
+    for (uint32_t y = 0; y < height; y++) {
+        for (uint32_t x = 0; x < width; x++) {
+            const float cr = re_min + (float)x * dre;
+            const float ci = im_min + (float)y * dim;
+            float zr = 0.0f, zi = 0.0f;
+            uint32_t k = 0;
+            while (k < max_iter) {
+                const float rr = zr * zr;
+                const float ii = zi * zi;
+                if (rr + ii > 4.0f) break;
+                const float nr = rr - ii + cr;
+                const float ni = (2.0f * zr) * zi + ci;
+                zr = nr;
+                zi = ni;
+                k++;
+            }
+            out[(uint64_t)y * width + x] = k;
+        }
+    }
+}

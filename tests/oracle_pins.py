@@ -237,6 +237,51 @@ def check_selectivity():
     assert _binom_ok(sizes[4], sizes[3], 2.0 / 3.0)
 
 
+def _one_point(cr, ci, max_iter):
+    """Escape count of the single point c = cr + ci i (a 1 x 1 image)."""
+    return int(oracle.mandelbrot(1, 1, cr, ci, cr + 1.0, ci + 1.0, max_iter)[0, 0])
+
+
+def check_mandelbrot_points():
+    """Escape counts that follow from the orbit of z <- z^2 + c by hand (all
+    values are small integers, exact in single precision), with the rule
+    "step while |z|^2 <= 4": c = 1: 0, 1, 2, 5 -> 3 steps; c = 2: 0, 2, 6 -> 2;
+    c = 3: 0, 3 -> 1; c = -2: 0, -2, 2, 2, ... stays on |z|^2 = 4 -> never
+    escapes; c = -1: 0, -1, 0, ... bounded; c = 0: bounded; c = i: 0, i, -1 + i,
+    -i, -1 + i, ... bounded; c = -i by symmetry; c = 1 + i: 0, 1 + i, 1 + 3i
+    (|z|^2 = 10) -> 2 steps; c = -1 + i: 0, -1 + i, -1 - i, -1 + 3i -> 3 steps;
+    c = 0.25 (the cusp, converges to 1/2) bounded."""
+    m = 50
+    cases = [((1.0, 0.0), 3), ((2.0, 0.0), 2), ((3.0, 0.0), 1), ((-2.0, 0.0), m), ((-1.0, 0.0), m),
+             ((0.0, 0.0), m), ((0.0, 1.0), m), ((0.0, -1.0), m), ((1.0, 1.0), 2), ((0.25, 0.0), m),
+             ((-3.0, 0.0), 1), ((0.0, 2.0), 2), ((-1.0, 1.0), 3)]
+    for (cr, ci), k in cases:
+        assert _one_point(cr, ci, m) == k, (cr, ci, _one_point(cr, ci, m), k)
+    assert _one_point(0.0, 0.0, 0) == 0 and _one_point(0.0, 0.0, 1) == 1
+
+
+def check_mandelbrot_image_properties():
+    """Image-level facts: pixel (x, y) is the point re_min + x dre, im_min + y dim
+    (a 1 x 1 image at that point gives the same count); conjugate points escape
+    after the same number of steps (negating ci negates every zi exactly); a
+    larger iteration limit only raises counts that reached the smaller limit."""
+    region = (-2.0, -1.25, 0.5, 1.25)
+    img = oracle.mandelbrot(40, 30, *region, 100)
+    assert img.shape == (30, 40) and img.max() == 100 and img.min() <= 3
+    dre = np.float32(np.float32(0.5 - -2.0) / np.float32(40))
+    dim = np.float32(np.float32(1.25 - -1.25) / np.float32(30))
+    for (x, y) in [(0, 0), (39, 29), (17, 11), (25, 3)]:
+        cr = float(np.float32(np.float32(-2.0) + np.float32(x) * dre))
+        ci = float(np.float32(np.float32(-1.25) + np.float32(y) * dim))
+        assert img[y, x] == _one_point(cr, ci, 100)
+    rng = np.random.default_rng(3)
+    for cr, ci in rng.uniform(-2.0, 1.0, size=(200, 2)).astype(np.float32):
+        assert _one_point(float(cr), float(ci), 200) == _one_point(float(cr), float(-ci), 200)
+    hi = oracle.mandelbrot(40, 30, *region, 300)
+    assert np.array_equal(np.minimum(hi, 100), img)
+
+
 ALL_PINS = [check_generator, check_predicate_values, check_compaction_exhaustive,
             check_compaction_small_exhaustive_values, check_compaction_library, check_scan,
-            check_three_phase, check_hash, check_interleave, check_selectivity]
+            check_three_phase, check_hash, check_interleave, check_selectivity, check_mandelbrot_points,
+            check_mandelbrot_image_properties]

@@ -12,6 +12,9 @@ import oracle_pins as pins
 SRC = os.path.join(os.path.dirname(oracle.__file__), "ka_oracle.c")
 
 MUTATIONS = {
+    "mandelbrot_no_doubling": ("const float ni = (2.0f * zr) * zi + ci;", "const float ni = zr * zi + ci;"),
+    "mandelbrot_escape_ge": ("if (rr + ii > 4.0f) break;", "if (rr + ii >= 4.0f) break;"),
+    "mandelbrot_sign": ("const float nr = rr - ii + cr;", "const float nr = rr + ii + cr;"),
     "inclusive_scan": ("        o[i] = running;\n        running += v[i];",
                        "        running += v[i];\n        o[i] = running;"),
     "lt_becomes_le": ("return x < param;", "return x <= param;"),
@@ -40,7 +43,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     mutated = tmp_path / "mut.c"
     mutated.write_text(src.replace(old, new, 1))
     so = tmp_path / "libmut.so"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", str(so), str(mutated)])
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so), str(mutated)])
     bad = oracle.bind(ctypes.CDLL(str(so)))
     oracle.lib()
     prev = oracle.use_library(bad)
