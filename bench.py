@@ -309,6 +309,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         result["extras"]["actor_vs_direct"] = actor_overhead(ka, torch)
         result["extras"]["microbench"] = microbench(ka, torch)
+        result["extras"]["mandelbrot"] = mandelbrot_large(ka, torch)
         result["extras"]["batch_4096"] = batch_large(ka, torch, peak)
         result["extras"]["serve"] = serve_large(ka, torch)
         sv = result["extras"]["serve"][0]
@@ -557,6 +558,54 @@ def microbench(ka, torch):
     finally:
         ka.ka_system_destroy(sysh, 1)
     del x
+    return out
+
+
+def mandelbrot_large(ka, torch, clocks_mhz=2070.0):
+    """The paper's compute workload (Sec. 5.4): escape-time images of the
+    rectangle -0.5 - 0.7375i .. 0.1 - 0.1375i at 1920 x 1080 (100 steps) and
+    16000 x 16000 (100 and 1000 steps). ALU-bound: a step is eight
+    single-precision adds and multiplies; the ceiling is one such operation
+    per FP32 lane per clock (152 SMs x 128 lanes x SM clock)."""
+    import numpy as np
+    region = (-0.5, -0.7375, 0.1, -0.1375)
+    st = torch.cuda.current_stream()
+    peak_ops = 152 * 128 * clocks_mhz * 1e6
+    out = []
+    for w, h, iters, reps in ((1920, 1080, 100, 20), (16000, 16000, 100, 3), (16000, 16000, 1000, 2)):
+        img = torch.empty(w * h, dtype=torch.int32, device="cuda")
+        ka.check(ka.ka_mandelbrot(img, w, h, *region, iters, st.cuda_stream))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            ka.check(ka.ka_mandelbrot(img, w, h, *region, iters, st.cuda_stream))
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        steps = float(img.to(torch.int64).sum().item())
+        achieved = 8.0 * steps / (ms * 1e-3)
+        out.append({"width": w, "height": h, "iterations": iters, "ms": round(ms, 3), "steps": steps,
+                    "steps/s": steps / (ms * 1e-3), "bound": "alu", "achieved_ops/s": achieved,
+                    "peak_ops/s": peak_ops, "frac": round(achieved / peak_ops, 4)})
+        del img
+    # actor against direct launch for the small image (request to result on the host)
+    s, sysh = ka.ka_system_create(0)
+    ka.check(s)
+    try:
+        s, a = ka.ka_spawn_stage(sysh, ka.KA_STAGE_MANDELBROT, 1920, 100, 1080)
+        ka.check(s)
+        msg = ka.make_msg()
+        ka.check(ka.ka_bench_request_loop(a, msg, 5, 1)[0])
+        s, ta, _ = ka.ka_bench_request_loop(a, msg, 100, 1)
+        ka.check(s)
+        s, td, _ = ka.ka_bench_direct_chain([(ka.KA_STAGE_MANDELBROT, 1920, 100, 1080)], None, 0, 100)
+        ka.check(s)
+        ka.ka_actor_release(a)
+    finally:
+        ka.ka_system_destroy(sysh, 1)
+    out.append({"actor_vs_direct": "1920 x 1080, 100 steps", "actor_us": round(ta * 1e4, 2),
+                "direct_us": round(td * 1e4, 2), "overhead_pct": round(100.0 * (ta / td - 1.0), 2)})
     return out
 
 

@@ -198,6 +198,16 @@ ka_status ka_compact_three_phase(const uint32_t *d_in, uint64_t n, const uint32_
                                  uint32_t param, uint32_t xform, uint32_t *d_out, uint32_t *d_count,
                                  void *d_ws, uint64_t ws_bytes, void *stream);
 
+/* Escape-time Mandelbrot image, the paper's compute workload (Sec. 5.4):
+ * d_out[y * width + x] = number of steps z <- z^2 + c taken from z = 0 while
+ * |z|^2 <= 4, at most max_iter, for c = (re_min + x dre, im_min + y dim),
+ * dre = (re_max - re_min) / width, dim = (im_max - im_min) / height, every
+ * operation a single-precision IEEE operation in that order (no fused
+ * multiply-add). The Mandelbrot actor stage uses the paper's rectangle
+ * -0.5 - 0.7375i .. 0.1 - 0.1375i. width * height < 2^32. */
+ka_status ka_mandelbrot(uint32_t *d_out, uint32_t width, uint32_t height, float re_min, float im_min,
+                        float re_max, float im_max, uint32_t max_iter, void *stream);
+
 /* Interleave of fuseFillsLiterals (Sec. 4.1, Listing 5): d_index[2i] =
  * d_chunk_ids[i], d_index[2i+1] = d_literals[i] for i < live k; d_n_out
  * (optional) receives 2 * live k. */
@@ -320,7 +330,9 @@ typedef enum ka_stage_kind {
     KA_STAGE_SCATTER = 4,   /* (x, f, o) -> (y)                                  */
     KA_STAGE_COMPACT = 5,   /* (x) -> (y)            fused single pass           */
     KA_STAGE_PREPARE = 6,   /* (a, b) -> (index)     interleave, 2k entries      */
-    KA_STAGE_EMPTY = 7      /* (x) -> (x)            empty kernel, overhead probe */
+    KA_STAGE_EMPTY = 7,     /* (x) -> (x)            empty kernel, overhead probe */
+    KA_STAGE_MANDELBROT = 8 /* () -> (image)         Sec. 5.4 region; pred = width,
+                               xform = height, param = iterations (see ka_mandelbrot) */
 } ka_stage_kind;
 
 typedef struct ka_stage_desc {

@@ -32,7 +32,7 @@ KA_PRED_AND_MASK_EQ0, KA_PRED_LT, KA_PRED_TOPBITS_LT, KA_PRED_POPC_ODD, KA_PRED_
 KA_XFORM_NONE, KA_XFORM_HASH = 0, 1
 KA_KERNEL_COMPACT, KA_KERNEL_SCAN, KA_KERNEL_BATCH = 0, 1, 2
 (KA_STAGE_GENERATE, KA_STAGE_MAP_HASH, KA_STAGE_PREDICATE, KA_STAGE_EXSCAN, KA_STAGE_SCATTER,
- KA_STAGE_COMPACT, KA_STAGE_PREPARE, KA_STAGE_EMPTY) = range(8)
+ KA_STAGE_COMPACT, KA_STAGE_PREPARE, KA_STAGE_EMPTY, KA_STAGE_MANDELBROT) = range(9)
 KA_U32 = 0
 KA_READ, KA_WRITE, KA_READ_WRITE = 1, 2, 3
 KA_MSG_MAX_REFS = 4
@@ -130,6 +130,8 @@ _SIGS = {
     "ka_three_phase_workspace_size": (ctypes.c_int32, [ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
     "ka_compact_three_phase": (ctypes.c_int32, [c_vp, ctypes.c_uint64, c_vp, ctypes.c_int32, ctypes.c_uint32,
                                                 ctypes.c_uint32, c_vp, c_vp, c_vp, ctypes.c_uint64, c_vp]),
+    "ka_mandelbrot": (ctypes.c_int32, [c_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_float, ctypes.c_float,
+                                       ctypes.c_float, ctypes.c_float, ctypes.c_uint32, c_vp]),
     "ka_prepare_index": (ctypes.c_int32, [c_vp, c_vp, ctypes.c_uint64, c_vp, c_vp, c_vp, c_vp]),
     "ka_batch_workspace_size": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(ka_tile),
                                                  ctypes.POINTER(ctypes.c_uint64)]),
@@ -290,6 +292,12 @@ def ka_compact_three_phase(d_in, n: int, d_n, pred: int, param: int, xform: int,
                            ws_bytes: int, stream=None) -> int:
     return lib.ka_compact_three_phase(ptr(d_in), n, ptr(d_n), pred, param, xform, ptr(d_out), ptr(d_count),
                                       ptr(d_ws), ws_bytes, stream_ptr(stream))
+
+
+def ka_mandelbrot(d_out, width: int, height: int, re_min: float, im_min: float, re_max: float, im_max: float,
+                  max_iter: int, stream=None) -> int:
+    return lib.ka_mandelbrot(ptr(d_out), width, height, re_min, im_min, re_max, im_max, max_iter,
+                             stream_ptr(stream))
 
 
 def ka_prepare_index(d_chunk_ids, d_literals, k: int, d_k, d_index, d_n_out=None, stream=None) -> int:

@@ -119,6 +119,11 @@ ka_status ka_bench_direct_chain(const ka_stage_desc *stages, uint32_t n_stages, 
             o.push_back(y);
             break;
         case KA_STAGE_EMPTY: o = cur; break;
+        case KA_STAGE_MANDELBROT:
+            if (d.pred <= 0 || d.xform == 0) s = KA_E_ARG;
+            if (s == KA_OK) s = alloc(uint64_t(d.pred) * d.xform, &y);
+            o.push_back(y);
+            break;
         default: s = KA_E_UNSUPPORTED;
         }
         if (s == KA_OK && (d.kind == KA_STAGE_PREDICATE || d.kind == KA_STAGE_COMPACT))
@@ -169,6 +174,10 @@ ka_status ka_bench_direct_chain(const ka_stage_desc *stages, uint32_t n_stages, 
                 e = launch_scatter(c[0].ptr, c[1].ptr, c[2].ptr, nn, np, o[0].ptr, o[0].count, st);
                 break;
             case KA_STAGE_EMPTY: e = launch_empty(st); break;
+            case KA_STAGE_MANDELBROT:  // the rectangle of the paper's workload (Sec. 5.4)
+                e = launch_mandelbrot(o[0].ptr, uint32_t(d.pred), d.xform, -0.5f, -0.7375f, 0.1f, -0.1375f, d.param,
+                                      o[0].count, st);
+                break;
             default: e = KA_E_UNSUPPORTED;
             }
             if (e != KA_OK) return e;

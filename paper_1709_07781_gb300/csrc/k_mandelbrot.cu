@@ -1,0 +1,79 @@
+// Escape-time Mandelbrot image: the paper's compute-bound workload for
+// kernel actors (Sec. 5.4), here a plain CUDA kernel and an actor stage.
+//
+// Pixel (x, y) is c = (re_min + x dre, im_min + y dim); from z = 0 the step
+// z <- z^2 + c is applied while |z|^2 <= 4, at most max_iter times, and the
+// pixel holds the number of steps. Every operation is one round-to-nearest
+// single-precision operation in a fixed order (__fmul_rn / __fadd_rn /
+// __fsub_rn cannot be contracted into fused multiply-adds), so each count is
+// reproducible bit for bit on any IEEE machine that does the same operations.
+//
+// The work is ALU-bound (eight single-precision adds and multiplies per
+// step, no memory traffic to speak of). Consecutive threads take consecutive
+// pixels of a row, whose orbits are alike, so a warp's lanes stay together.
+#include "ka_internal.h"
+
+namespace ka {
+namespace {
+
+constexpr int kMbBlock = 256;
+
+__global__ void __launch_bounds__(kMbBlock) k_mandelbrot(uint32_t *out, uint32_t width, uint64_t pixels, float re_min,
+                                                          float im_min, float dre, float dim, uint32_t max_iter) {
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t p = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < pixels; p += stride) {
+        const uint32_t y = uint32_t(p / width), x = uint32_t(p - uint64_t(y) * width);
+        const float cr = __fadd_rn(re_min, __fmul_rn(float(x), dre));
+        const float ci = __fadd_rn(im_min, __fmul_rn(float(y), dim));
+        float zr = 0.0f, zi = 0.0f;
+        uint32_t k = 0;
+        while (k < max_iter) {
+            const float rr = __fmul_rn(zr, zr);
+            const float ii = __fmul_rn(zi, zi);
+            if (__fadd_rn(rr, ii) > 4.0f) break;
+            const float nr = __fadd_rn(__fsub_rn(rr, ii), cr);
+            const float ni = __fadd_rn(__fmul_rn(__fmul_rn(2.0f, zr), zi), ci);
+            zr = nr;
+            zi = ni;
+            ++k;
+        }
+        out[p] = k;
+    }
+}
+
+__global__ void k_set_word(uint32_t *w, uint32_t v) { *w = v; }
+
+}  // namespace
+
+ka_status launch_mandelbrot(uint32_t *out, uint32_t width, uint32_t height, float re_min, float im_min, float re_max,
+                            float im_max, uint32_t max_iter, uint32_t *n_out, cudaStream_t stream) {
+    const uint64_t pixels = uint64_t(width) * height;
+    if (pixels > 0xFFFFFFFFull || (pixels && !out)) return KA_E_ARG;
+    if (pixels) {
+        // the same single-precision expressions as the definition
+        const float dre = (re_max - re_min) / float(width);
+        const float dim = (im_max - im_min) / float(height);
+        uint64_t blocks = (pixels + kMbBlock - 1) / kMbBlock;
+        const uint64_t cap = uint64_t(device_info().sm_count) * 16;
+        if (blocks > cap) blocks = cap;
+        k_mandelbrot<<<unsigned(blocks), kMbBlock, 0, stream>>>(out, width, pixels, re_min, im_min, dre, dim,
+                                                                max_iter);
+        const ka_status s = cuda_status(cudaGetLastError());
+        if (s != KA_OK) return s;
+    }
+    if (n_out) {
+        k_set_word<<<1, 1, 0, stream>>>(n_out, uint32_t(pixels));
+        return cuda_status(cudaGetLastError());
+    }
+    return KA_OK;
+}
+
+}  // namespace ka
+
+using namespace ka;
+
+extern "C" ka_status ka_mandelbrot(uint32_t *d_out, uint32_t width, uint32_t height, float re_min, float im_min,
+                                   float re_max, float im_max, uint32_t max_iter, void *stream) {
+    return launch_mandelbrot(d_out, width, height, re_min, im_min, re_max, im_max, max_iter, nullptr,
+                             static_cast<cudaStream_t>(stream));
+}

@@ -159,6 +159,7 @@ struct StageSpec {
     uint32_t mul = 1;
     ka_tile tile{0, 0};
     int in_arity = 1, out_arity = 1;
+    uint32_t width = 0, height = 0, iters = 0;  // KA_STAGE_MANDELBROT
 };
 
 struct Actor {
@@ -447,6 +448,16 @@ static ka_status run_stage(System *s, const StageSpec &sp, Msg *m, Ref **outs, i
         Ref *y;
         if ((e = new_owned_ref(s, m->gen_n, &y)) != KA_OK) return e;
         e = launch_generate(static_cast<uint32_t *>(y->ptr), m->gen_n, m->seed, y->d_count, st);
+        outs[(*n_outs)++] = y;
+        return e;
+    }
+    case KA_STAGE_MANDELBROT: {
+        Ref *y;
+        const uint64_t pixels = uint64_t(sp.width) * sp.height;
+        if ((e = new_owned_ref(s, pixels, &y)) != KA_OK) return e;
+        // the rectangle of the paper's workload (Sec. 5.4)
+        e = launch_mandelbrot(static_cast<uint32_t *>(y->ptr), sp.width, sp.height, -0.5f, -0.7375f, 0.1f, -0.1375f,
+                              sp.iters, y->d_count, st);
         outs[(*n_outs)++] = y;
         return e;
     }
@@ -999,6 +1010,14 @@ ka_status ka_spawn_stage(ka_system *h, const ka_stage_desc *d, ka_actor **out) {
         break;
     case KA_STAGE_PREPARE: sp.in_arity = 2; sp.out_arity = 1; break;
     case KA_STAGE_EMPTY: sp.in_arity = 1; sp.out_arity = 1; break;
+    case KA_STAGE_MANDELBROT:
+        sp.width = uint32_t(d->pred);
+        sp.height = d->xform;
+        sp.iters = d->param;
+        if (d->pred <= 0 || d->xform == 0 || uint64_t(sp.width) * sp.height > 0xFFFFFFFFull) return KA_E_ARG;
+        sp.in_arity = 0;
+        sp.out_arity = 1;
+        break;
     default: return KA_E_ARG;
     }
     Actor *a = new Actor;
