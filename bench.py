@@ -729,7 +729,7 @@ def serve_large(ka, torch):
             reqs = ka.serve_requests(tr.arrival_s, tr.n, tr.seeds, stages)
             row = {"rate_per_s": rate, "duration_s": dur, "requests": len(tr.n),
                    "offered_elements/s": float(np.sum(tr.n)) / dur}
-            for mode, name in ((0, "batched"), (1, "plain")):
+            for mode, name in ((0, "batched"), (1, "plain"), (2, "batched_no_graph")):
                 s, res, stats = ka.serve(sysh, reqs, mode=mode)
                 ka.check(s)
                 lat = np.array([res[r].done_s - tr.arrival_s[r] for r in range(len(tr.n))])
@@ -738,7 +738,7 @@ def serve_large(ka, torch):
                              "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
                              "p999_ms": round(1e3 * float(np.percentile(lat, 99.9)), 3),
                              "launches": int(stats.launches), "iterations": int(stats.iterations),
-                             "peak_GB": round(stats.peak_bytes / 1e9, 3),
+                             "peak_GB": round(stats.peak_bytes / 1e9, 3), "graph_launches": int(stats.graph_launches),
                              "ok": all(res[r].status == 0 for r in range(len(tr.n)))}
             out.append(row)
     finally:

@@ -441,7 +441,9 @@ typedef struct ka_serve_result {
 } ka_serve_result;
 
 typedef struct ka_serve_options {
-    uint32_t mode;               /* 0: continuous batching; 1: plain launches per request */
+    uint32_t mode;               /* 0: continuous batching, each tick one CUDA graph launch;
+                                    1: plain launches per request; 2: continuous
+                                    batching with the tick's launches issued directly */
     uint32_t max_inflight;       /* admitted requests at most (0: 4096)              */
     uint64_t budget_bytes;       /* admission budget (0: the system's)               */
     double time_scale;           /* arrival_s multiplier (1.0 = real time)           */
@@ -456,6 +458,7 @@ typedef struct ka_serve_stats {
     uint64_t peak_bytes;         /* peak admitted bytes                              */
     uint32_t max_inflight_seen;
     uint32_t rejected;           /* requests larger than the whole budget            */
+    uint64_t graph_launches;     /* ticks issued as one CUDA graph launch (mode 0)   */
 } ka_serve_stats;
 
 ka_status ka_serve_run(ka_system *sys, const ka_serve_request *reqs, uint32_t n_reqs,

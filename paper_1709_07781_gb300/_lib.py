@@ -104,7 +104,8 @@ class ka_serve_options(ctypes.Structure):
 class ka_serve_stats(ctypes.Structure):
     _fields_ = [("wall_s", ctypes.c_double), ("elements", ctypes.c_uint64), ("launches", ctypes.c_uint64),
                 ("iterations", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
-                ("max_inflight_seen", ctypes.c_uint32), ("rejected", ctypes.c_uint32)]
+                ("max_inflight_seen", ctypes.c_uint32), ("rejected", ctypes.c_uint32),
+                ("graph_launches", ctypes.c_uint64)]
 
 
 MONITOR_FN = ctypes.CFUNCTYPE(None, c_vp, ctypes.c_int32)

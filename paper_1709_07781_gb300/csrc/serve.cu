@@ -17,6 +17,10 @@
 // waiting for the running ones to finish and their work overlaps on the
 // device. Descriptor tables are double-buffered per tick slot.
 //
+// In mode 0 each tick slot's sequence is captured once per depth as a CUDA
+// graph (tables of kTickItems entries, the unused ones empty) and a tick is
+// one graph launch; mode 2 issues the same ticks as separate calls.
+//
 // Mode 1, plain launches: the same admission, but every request is issued on
 // arrival as its own launches (generate, then one compaction per stage).
 //
@@ -24,6 +28,7 @@
 // buffers from their own stream-ordered memory pool.
 #include <algorithm>
 #include <chrono>
+#include <cstring>
 #include <deque>
 #include <thread>
 #include <vector>
@@ -49,6 +54,10 @@ struct Tick {
     std::vector<uint32_t> reqs;  // request indices, tick position = vector index
     uint32_t depth = 0;          // stages of the deepest request
     bool busy = false;
+    // graph mode: the tick's whole sequence for each depth, captured once;
+    // host table entries past the current tick are kept zero (empty items)
+    cudaGraphExec_t graph[kDepth] = {nullptr, nullptr, nullptr, nullptr};
+    uint32_t hw_gen = 0, hw_items[kDepth] = {0, 0, 0, 0};  // entries written by the previous tick
 
     static constexpr size_t kGenOff = 0;
     static constexpr size_t kItemsOff = kGenOff + sizeof(ka_gen_item) * kTickItems;
@@ -99,6 +108,7 @@ struct Run {
     uint64_t ws_gen_bytes = 0, ws_cmp_bytes = 0;
     ka_tile batch_tile{0, 0};
     uint32_t grid_max = 0;  // blocks of a full persistent launch
+    bool graphs = false;    // ticks replay captured graphs
 
     // plain mode
     struct Slot {
@@ -217,6 +227,27 @@ ka_status issue_tick(Run &R, bool *issued) {
         }
     }
     cudaStream_t st = R.stream;
+    if (R.graphs) {
+        // zero the entries the previous tick used beyond this one's, then replay
+        if (T.hw_gen > k) std::memset(T.gen(T.host) + k, 0, sizeof(ka_gen_item) * (T.hw_gen - k));
+        T.hw_gen = k;
+        for (uint32_t d = 0; d < T.depth; ++d) {
+            if (T.hw_items[d] > per_stage[d])
+                std::memset(T.items(T.host, int(d)) + per_stage[d], 0,
+                            sizeof(ka_batch_item) * (T.hw_items[d] - per_stage[d]));
+            T.hw_items[d] = per_stage[d];
+        }
+        ka_status s = cuda_status(cudaGraphLaunch(T.graph[T.depth - 1], st));
+        R.st.launches += 2 + 2 * T.depth;
+        R.st.graph_launches += 1;
+        if (s == KA_OK) s = cuda_status(cudaEventRecord(T.ev, st));
+        if (s != KA_OK) return s;
+        T.busy = true;
+        R.tick_used += 1;
+        R.st.iterations += 1;
+        *issued = true;
+        return KA_OK;
+    }
     ka_status s = cuda_status(
         cudaMemcpyAsync(T.gen(T.dev), T.gen(T.host), sizeof(ka_gen_item) * k, cudaMemcpyHostToDevice, st));
     for (uint32_t d = 0; d < T.depth && s == KA_OK; ++d)
@@ -243,6 +274,59 @@ ka_status issue_tick(Run &R, bool *issued) {
     R.st.iterations += 1;
     *issued = true;
     return KA_OK;
+}
+
+// The device work of a tick of `depth` stages over full tables (kTickItems
+// entries each, the unused ones empty), on the run's stream: what a tick
+// graph holds.
+ka_status full_tick_ops(Run &R, Tick &T, uint32_t depth) {
+    cudaStream_t st = R.stream;
+    ka_status s = cuda_status(cudaMemcpyAsync(T.gen(T.dev), T.gen(T.host), sizeof(ka_gen_item) * kTickItems,
+                                              cudaMemcpyHostToDevice, st));
+    for (uint32_t d = 0; d < depth && s == KA_OK; ++d)
+        s = cuda_status(cudaMemcpyAsync(T.items(T.dev, int(d)), T.items(T.host, int(d)),
+                                        sizeof(ka_batch_item) * kTickItems, cudaMemcpyHostToDevice, st));
+    if (s == KA_OK) s = ka_generate_batch(T.gen(T.dev), kTickItems, kTickItems, R.ws_gen, R.ws_gen_bytes, st);
+    for (uint32_t d = 0; d < depth && s == KA_OK; ++d)
+        s = ka_compact_batch(T.items(T.dev, int(d)), kTickItems, kTickItems, R.ws_cmp, R.ws_cmp_bytes, &R.batch_tile,
+                             0, st);
+    if (s == KA_OK)
+        s = cuda_status(cudaMemcpyAsync(T.cnt(T.host, 0), T.cnt(T.dev, 0), sizeof(uint32_t) * kTickItems * depth,
+                                        cudaMemcpyDeviceToHost, st));
+    if (s == KA_OK)
+        s = cuda_status(cudaMemcpyAsync(T.err(T.host), &static_cast<WsHeader *>(R.ws_cmp)->error, 4,
+                                        cudaMemcpyDeviceToHost, st));
+    return s;
+}
+
+// Captures every tick slot's graph for depths 1..kDepth. The kernels run
+// once first outside any capture (their launch set-up happens then). On any
+// failure the run keeps issuing ticks directly.
+void build_graphs(Run &R) {
+    R.graphs = false;
+    if (full_tick_ops(R, R.ticks[0], kDepth) != KA_OK || cudaStreamSynchronize(R.stream) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    for (Tick &T : R.ticks) {
+        for (uint32_t d = 1; d <= uint32_t(kDepth); ++d) {
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(R.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                cudaGetLastError();
+                return;
+            }
+            const ka_status s = full_tick_ops(R, T, d);
+            const cudaError_t e = cudaStreamEndCapture(R.stream, &g);
+            if (s != KA_OK || e != cudaSuccess || !g ||
+                cudaGraphInstantiate(&T.graph[d - 1], g, 0) != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
+                return;
+            }
+            cudaGraphDestroy(g);
+        }
+    }
+    R.graphs = true;
 }
 
 ka_status poll_ticks(Run &R, bool *progressed) {
@@ -341,7 +425,7 @@ ka_status setup(Run &R, uint32_t max_n) {
     if (s != KA_OK) return s;
     uint64_t keep = ~0ull;  // keep freed memory in the pool for the next requests
     cudaMemPoolSetAttribute(R.pool, cudaMemPoolAttrReleaseThreshold, &keep);
-    if (R.mode == 0) {
+    if (R.mode != 1) {
         R.batch_tile = resolve_tile(KA_KERNEL_BATCH, kBatchTileKey, R.tile.block ? &R.tile : nullptr);
         R.grid_max = uint32_t(device_info().sm_count) * 8;
         s = ka_batch_workspace_size(kTickItems, 0, nullptr, &R.ws_gen_bytes);
@@ -357,7 +441,9 @@ ka_status setup(Run &R, uint32_t max_n) {
             if (s == KA_OK) s = cuda_status(cudaHostAlloc(&R.ticks[i].host, Tick::kBytes, cudaHostAllocDefault));
             if (s == KA_OK) s = cuda_status(cudaEventCreateWithFlags(&R.ticks[i].ev, cudaEventDisableTiming));
             if (s == KA_OK) s = cuda_status(cudaMemsetAsync(R.ticks[i].dev, 0, Tick::kBytes, R.stream));
+            if (s == KA_OK) std::memset(R.ticks[i].host, 0, Tick::kBytes);  // zero entries are empty items
         }
+        if (s == KA_OK && R.mode == 0) build_graphs(R);
     } else {
         const uint32_t slots = R.max_inflight;
         s = ka_workspace_size(max_n ? max_n : 1, nullptr, &R.ws_plain_bytes);
@@ -384,6 +470,8 @@ void teardown(Run &R) {
         }
     if (R.stream) cudaStreamSynchronize(R.stream);
     for (Tick &T : R.ticks) {
+        for (cudaGraphExec_t &g : T.graph)
+            if (g) cudaGraphExecDestroy(g);
         if (T.dev) cudaFree(T.dev);
         if (T.host) cudaFreeHost(T.host);
         if (T.ev) cudaEventDestroy(T.ev);
@@ -408,7 +496,7 @@ using namespace ka;
 extern "C" ka_status ka_serve_run(ka_system *sys, const ka_serve_request *reqs, uint32_t n_reqs,
                                   const ka_serve_options *opt, ka_serve_result *results, ka_serve_stats *stats) {
     if (!sys || !opt || (n_reqs && (!reqs || !results))) return KA_E_ARG;
-    if (opt->mode > 1) return KA_E_ARG;
+    if (opt->mode > 2) return KA_E_ARG;
     int device = 0;
     uint64_t sys_budget = 0;
     ka_status s = system_exec_info(sys, &device, &sys_budget);
@@ -416,7 +504,7 @@ extern "C" ka_status ka_serve_run(ka_system *sys, const ka_serve_request *reqs, 
     s = cuda_status(cudaSetDevice(device));
     if (s != KA_OK) return s;
     if (opt->tile.block || opt->tile.ipt) {
-        const int32_t k = opt->mode == 0 ? KA_KERNEL_BATCH : KA_KERNEL_COMPACT;
+        const int32_t k = opt->mode == 1 ? KA_KERNEL_COMPACT : KA_KERNEL_BATCH;
         if (!tile_supported_for(k, opt->tile.block, opt->tile.ipt)) return KA_E_ARG;
     }
     Run R;
@@ -455,10 +543,10 @@ extern "C" ka_status ka_serve_run(ka_system *sys, const ka_serve_request *reqs, 
                 R.waiting.push_back(r);
             }
             bool done_some = false, issued = false;
-            s = R.mode == 0 ? poll_ticks(R, &done_some) : poll_plain(R, &done_some);
-            if (s == KA_OK) s = R.mode == 0 ? issue_tick(R, &issued) : issue_plain(R, &issued);
+            s = R.mode != 1 ? poll_ticks(R, &done_some) : poll_plain(R, &done_some);
+            if (s == KA_OK) s = R.mode != 1 ? issue_tick(R, &issued) : issue_plain(R, &issued);
             if (s != KA_OK) break;
-            const bool busy = R.mode == 0 ? R.tick_used > 0 : !R.plain_inflight.empty();
+            const bool busy = R.mode != 1 ? R.tick_used > 0 : !R.plain_inflight.empty();
             if (!done_some && !issued) {
                 if (!busy && R.waiting.empty() && R.next < R.n) {
                     // idle until the next arrival (sleep coarsely, then spin)

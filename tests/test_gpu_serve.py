@@ -50,7 +50,7 @@ def expected(tr, r):
     return y, len(y)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_every_result_matches_the_oracle(ka, system, mode):
     tr, stages, reqs = trace(ka, 4000.0, 0.1, 8, 18)
     n = len(tr.n)
@@ -71,10 +71,14 @@ def test_every_result_matches_the_oracle(ka, system, mode):
         assert res[r].done_s >= res[r].admit_s >= tr.arrival_s[r] - 1e-3
         if r in outs:
             assert np.array_equal(outs[r][:k], y) and outs[r][k] == 0
-    if mode == 0:
+    if mode != 1:
         assert stats.iterations < n  # requests shared batched launches
     else:
         assert stats.iterations == n
+    if mode == 0:
+        assert stats.graph_launches == stats.iterations  # every tick was one graph launch
+    else:
+        assert stats.graph_launches == 0
 
 
 def test_same_result_alone_and_in_the_mix(ka, system):
