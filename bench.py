@@ -39,7 +39,7 @@ SELECTIVITIES = (0.01, 0.5, 0.99)
 SEED = 2
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1709_07781_gb300", "csrc", f)
-                  for f in ("k_compact_tma.cu", "ka_dev.cuh")]
+                  for f in ("k_compact_tma.cu", "ka_tma.cuh", "ka_dev.cuh")]
 TMA_SHAPES = ((256, 16), (512, 16), (768, 16))
 
 
@@ -56,6 +56,9 @@ def parse_args():
     p.add_argument("--tile", default="", help="block,ipt: fix the tile shape instead of autotuning it")
     p.add_argument("--clock-interval-ms", type=int, default=100,
                    help="nvidia-smi sampling interval during the timed region (0: do not sample)")
+    p.add_argument("--only", choices=["", "scan", "batch"], default="",
+                   help="time one kernel alone (for profiling): the exclusive scan of --n flags, or the "
+                        "4096-instance batch; W warm-up and K timed launches")
     return p.parse_args()
 
 
@@ -798,8 +801,82 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_only(args):
+    """One kernel alone, W warm-up then K timed launches on the default stream
+    (the command the committed ncu summaries of these kernels were taken on)."""
+    import numpy as np
+    import torch
+    import paper_1709_07781_gb300 as ka
+    import ka_inputs as ki
+    st = torch.cuda.current_stream()
+    tile = tuple(int(v) for v in args.tile.split(",")) if args.tile else None
+    W, K = max(args.warmup, 3), args.steps
+    if args.only == "scan":
+        N = args.n
+        x = torch.empty(N, dtype=torch.int32, device="cuda")
+        ka.check(ka.ka_generate(x, N, SEED, st.cuda_stream))
+        f = torch.empty_like(x)
+        ka.check(ka.ka_predicate(x, N, None, ka.KA_PRED_LT, 1 << 31, f, st.cuda_stream))
+        del x
+        o, tot = torch.empty_like(f), torch.zeros(4, dtype=torch.int32, device="cuda")
+        s, wsb = ka.ka_workspace_size(N)
+        ka.check(s)
+        ws_t = torch.empty(wsb + 256, dtype=torch.uint8, device="cuda")
+        ws = (ws_t.data_ptr() + 255) // 256 * 256
+        ka.check(ka.ka_workspace_init(ws, wsb, st.cuda_stream))
+
+        def launch():
+            ka.check(ka.ka_exclusive_scan(f, N, None, o, tot, ws, wsb, tile, st.cuda_stream))
+        units, bytes_ = N, 8.0 * N
+    else:
+        spec = ki.config_batch()
+        m = len(spec.n)
+        n = spec.n.astype(np.int64)
+        offs = np.concatenate([[0], np.cumsum((n + 3) // 4 * 4)])
+        total = int(offs[-1])
+        x = torch.empty(total, dtype=torch.int32, device="cuda")
+        y = torch.empty_like(x)
+        cnt = torch.zeros(m, dtype=torch.int32, device="cuda")
+        gen, items = (ka.ka_gen_item * m)(), (ka.ka_batch_item * m)()
+        for i in range(m):
+            gen[i] = ka.ka_gen_item(x.data_ptr() + 4 * int(offs[i]), int(spec.seeds[i]), int(n[i]), 0)
+            items[i] = ka.ka_batch_item(x.data_ptr() + 4 * int(offs[i]), y.data_ptr() + 4 * int(offs[i]), None,
+                                        cnt.data_ptr() + 4 * i, int(n[i]), ka.KA_PRED_LT, int(spec.t[i]), 0)
+        d_gen = torch.frombuffer(bytearray(bytes(gen)), dtype=torch.uint8).cuda()
+        d_items = torch.frombuffer(bytearray(bytes(items)), dtype=torch.uint8).cuda()
+        s, wsb = ka.ka_batch_workspace_size(m, total, None)
+        ka.check(s)
+        ws_t = torch.empty(wsb + 256, dtype=torch.uint8, device="cuda")
+        ws = (ws_t.data_ptr() + 255) // 256 * 256
+        ka.check(ka.ka_workspace_init(ws, wsb, st.cuda_stream))
+        ka.check(ka.ka_generate_batch(d_gen, m, m, ws, wsb, st.cuda_stream))
+
+        def launch():
+            ka.check(ka.ka_compact_batch(d_items, m, m, ws, wsb, tile, 0, st.cuda_stream))
+        units, bytes_ = int(n.sum()), None
+    for _ in range(W):
+        launch()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(K):
+        launch()
+    e1.record(st)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1000.0 / K
+    if bytes_ is None:
+        bytes_ = 4.0 * units + 4.0 * float(cnt.cpu().numpy().view(np.uint32).astype(np.int64).sum())
+    peak, peak_kind = measured_peak_gbs()
+    print(json.dumps({"only": args.only, "tile": list(tile) if tile else None, "units": units, "us": round(us, 2),
+                      "GB/s": round(bytes_ / us / 1e3, 1), "frac": round(bytes_ / us / 1e3 / peak, 4),
+                      "peak_kind": peak_kind}), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.only:
+        run_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
