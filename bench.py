@@ -39,7 +39,7 @@ SELECTIVITIES = (0.01, 0.5, 0.99)
 SEED = 2
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1709_07781_gb300", "csrc", f)
-                  for f in ("k_compact_tma.cu", "ka_tma.cuh", "ka_dev.cuh")]
+                  for f in ("ka_tma_pass.cuh", "k_compact_tma.cu", "k_tma_768.cu", "ka_tma.cuh", "ka_dev.cuh")]
 TMA_SHAPES = ((256, 16), (512, 16), (768, 16))
 
 
