@@ -42,7 +42,7 @@ struct TileInfo {  // one per stage
 
 template <int CWW, int S, int LAG, int MAXG, int MINB>
 __global__ void __launch_bounds__((CWW + 2) * 32, MINB) k_batch_tma(const BatchArgs a) {
-    constexpr int T = CWW * kSeg, ROWS = 4;
+    constexpr int T = CWW * kSeg;
     constexpr int K = (MAXG + 31) / 32;
     static_assert(LAG >= 1 && LAG < S && LAG <= 3, "a stage is written out before its refill; slots repeat every 4");
     static_assert(CWW <= 32, "the look-back warp holds one segment count per lane");
@@ -224,46 +224,15 @@ __global__ void __launch_bounds__((CWW + 2) * 32, MINB) k_batch_tma(const BatchA
             const uint32_t vhi = ti.vhi > base ? min(ti.vhi - base, uint32_t(kSeg)) : 0u;
             uint32_t rowbase = 0;
             if (vhi > vlo) {
-                uint32_t v[ROWS][4], m[ROWS], packed = 0;
-#pragma unroll
-                for (int r = 0; r < ROWS; ++r) {
-                    const uint32_t e0 = uint32_t(r * 128 + lane * 4);
-                    const uint4 q = *reinterpret_cast<const uint4 *>(seg + e0);
-                    v[r][0] = q.x;
-                    v[r][1] = q.y;
-                    v[r][2] = q.z;
-                    v[r][3] = q.w;
-                }
-                if (mul != 1u) {
-#pragma unroll
-                    for (int r = 0; r < ROWS; ++r)
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) v[r][c] *= mul;
-                }
-#pragma unroll
-                for (int r = 0; r < ROWS; ++r) {
-                    const uint32_t e0 = uint32_t(r * 128 + lane * 4);
-                    uint32_t mk = pred_mask4(ti.pred, v[r][0], v[r][1], v[r][2], v[r][3]);
-                    if (vlo != 0u || vhi != uint32_t(kSeg)) {
-                        const uint32_t skip = vlo > e0 ? min(vlo - e0, 4u) : 0u;
-                        const uint32_t left = vhi > e0 ? vhi - e0 : 0u;
-                        mk &= (0xFu << skip) & (left >= 4 ? 0xFu : ((1u << left) - 1u));
-                    }
-                    m[r] = mk;
-                    packed += uint32_t(__popc(mk)) << (8 * r);
-                }
-                const uint32_t incl = warp_incl_scan(packed, lane);
-                const uint32_t excl = incl - packed;
-                const uint32_t rows = __shfl_sync(kFull, incl, 31);
-                __syncwarp();  // every lane holds its entries before any is overwritten
-#pragma unroll
-                for (int r = 0; r < ROWS; ++r) {
-                    uint32_t pos = rowbase + ((excl >> (8 * r)) & 0xFFu);
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        if ((m[r] >> c) & 1u) seg[pos++] = v[r][c];
-                    }
-                    rowbase += (rows >> (8 * r)) & 0xFFu;
+                // the tile's item fixes the predicate: one branch per tile into
+                // a count loop made for that predicate kind
+                switch (ti.pred.kind) {
+                case kAndMaskEq0: rowbase = compact_segment<kAndMaskEq0>(seg, ti.pred, mul, vlo, vhi, lane); break;
+                case kLt: rowbase = compact_segment<kLt>(seg, ti.pred, mul, vlo, vhi, lane); break;
+                case kPopcOdd: rowbase = compact_segment<kPopcOdd>(seg, ti.pred, mul, vlo, vhi, lane); break;
+                case kModNe0: rowbase = compact_segment<kModNe0>(seg, ti.pred, mul, vlo, vhi, lane); break;
+                case kNe: rowbase = compact_segment<kNe>(seg, ti.pred, mul, vlo, vhi, lane); break;
+                default: rowbase = compact_segment<kAll>(seg, ti.pred, mul, vlo, vhi, lane); break;
                 }
             }
             if (lane == 0) {

@@ -64,6 +64,68 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 constexpr int kSeg = 512;         // entries per compute warp and tile (32 lanes x 4 rows x 4)
 
 
+// The 4-entry keep mask for predicate kind PK (-1: the kind in p, chosen at
+// run time).
+template <int PK>
+__device__ __forceinline__ uint32_t mask4_of(const PredDev &p, uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3) {
+    if constexpr (PK < 0) return pred_mask4(p, x0, x1, x2, x3);
+    else if constexpr (PK == kAll) return 0xFu;
+    else return mask4_k<PK>(p, x0, x1, x2, x3);
+}
+
+// One warp counts the kept entries of its 512-entry segment (entries
+// [vlo, vhi) are input entries; the others are ignored) and compacts them in
+// place at the segment's front, in order. Returns the count.
+template <int PK>
+__device__ __forceinline__ uint32_t compact_segment(uint32_t *seg, const PredDev &pred, uint32_t mul, uint32_t vlo,
+                                                    uint32_t vhi, int lane) {
+    constexpr int ROWS = 4;
+    uint32_t v[ROWS][4], m[ROWS], packed = 0;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        const uint32_t e0 = uint32_t(r * 128 + lane * 4);
+        const uint4 q = *reinterpret_cast<const uint4 *>(seg + e0);
+        v[r][0] = q.x;
+        v[r][1] = q.y;
+        v[r][2] = q.z;
+        v[r][3] = q.w;
+    }
+    if (mul != 1u) {
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[r][c] *= mul;
+    }
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        const uint32_t e0 = uint32_t(r * 128 + lane * 4);
+        uint32_t mk = mask4_of<PK>(pred, v[r][0], v[r][1], v[r][2], v[r][3]);
+        if (vlo != 0u || vhi != uint32_t(kSeg)) {
+            const uint32_t skip = vlo > e0 ? min(vlo - e0, 4u) : 0u;
+            const uint32_t left = vhi > e0 ? vhi - e0 : 0u;
+            mk &= (0xFu << skip) & (left >= 4 ? 0xFu : ((1u << left) - 1u));
+        }
+        m[r] = mk;
+        packed += uint32_t(__popc(mk)) << (8 * r);
+    }
+    // per-row counts, 8 bits each (a row of the warp keeps at most 128)
+    const uint32_t incl = warp_incl_scan(packed, lane);
+    const uint32_t excl = incl - packed;
+    const uint32_t rows = __shfl_sync(kFull, incl, 31);
+    __syncwarp();  // every lane holds its entries before any is overwritten
+    uint32_t rowbase = 0;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        uint32_t pos = rowbase + ((excl >> (8 * r)) & 0xFFu);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if ((m[r] >> c) & 1u) seg[pos++] = v[r][c];
+        }
+        rowbase += (rows >> (8 * r)) & 0xFFu;
+    }
+    return rowbase;
+}
+
 // One warp copies cnt compacted entries from shared memory (16-byte aligned)
 // to dst (4-byte aligned): single entries up to dst's next 16-byte boundary,
 // then 16-byte stores, each assembled from two aligned 16-byte shared loads,

@@ -60,15 +60,6 @@ struct TmaArgs {
     PredDev pred;
 };
 
-// The 4-entry keep mask for predicate kind PK (-1: the kind in p, chosen at
-// run time).
-template <int PK>
-__device__ __forceinline__ uint32_t mask4_of(const PredDev &p, uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3) {
-    if constexpr (PK < 0) return pred_mask4(p, x0, x1, x2, x3);
-    else if constexpr (PK == kAll) return 0xFu;
-    else return mask4_k<PK>(p, x0, x1, x2, x3);
-}
-
 // One pass of the warp-specialised kernel. SCAN = false: fused compaction
 // with predicate kind PK (a PredKind, or -1: any kind, chosen at run time)
 // (count, compact in place, write out the kept entries). SCAN = true:
