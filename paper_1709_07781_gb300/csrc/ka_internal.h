@@ -72,8 +72,8 @@ struct CompactLaunch {
     ka_tile tile;
 };
 ka_status launch_compact(const CompactLaunch &L, cudaStream_t stream);
-// The warp-specialised TMA kernel (16-byte-aligned input, tile ipt 16 with
-// 256 or 512 threads); launch_compact routes to it when eligible.
+// The warp-specialised TMA kernel (the TMA shapes, any 4-byte-aligned input
+// of up to 2^32 - 4 entries); launch_compact routes to it when eligible.
 bool compact_tma_eligible(const CompactLaunch &L);
 ka_status launch_compact_tma(const CompactLaunch &L, cudaStream_t stream);
 
