@@ -151,3 +151,79 @@ def test_full_size_2_28(ka, s, shape):
     y, ek = oracle.compact(x, "lt", t)
     assert k == ek
     assert np.array_equal(to_host(out, k), y)
+
+
+@pytest.mark.parametrize("what", ["compact", "scan", "batch"])
+def test_tma_lookback_timeout_reports_status(ka, what):
+    """A look-back whose predecessors never publish gives up after the spin
+    limit and reports KA_E_DEVICE_TIMEOUT; the launch ends and the context
+    stays usable. The missing publications are made on the host: the
+    workspace's ticket count is set one short of the grid, so the first block
+    to arrive draws the launch's last ticket and resets the count to the next
+    epoch. Blocks whose tickets land after that reset run in the next epoch,
+    and neither side accepts the other's status words (every access stays in
+    bounds and every wait is bounded). Whether a block lands before or after
+    the reset depends on the order in which the tickets reach memory, so the
+    launch is repeated, the workspace re-initialised each time, until one
+    splits; a launch that does not split must give the right result."""
+    n = (1 << 22) + 5
+    shape = (768, 16) if what != "scan" else (512, 16)
+    # the persistent grid: one block per SM for (768, 16), two for (512, 16)
+    per_sm = {768: 1, 512: 2}[shape[0]]
+    tiles = (n + shape[0] * shape[1] - 1) // (shape[0] * shape[1])
+    G = min(tiles, torch.cuda.get_device_properties(0).multi_processor_count * per_sm)
+    assert G > 1
+    x = ki.uniform_u32(8, n)
+    d_x = to_dev(x)
+    out, count = empty(n + 16), empty(1)
+    if what == "batch":
+        items = np.zeros(1, dtype=[("in_", "<u8"), ("out", "<u8"), ("n_ptr", "<u8"), ("count", "<u8"), ("n", "<u4"),
+                                   ("pred", "<i4"), ("param", "<u4"), ("xform", "<u4")])
+        items[0] = (d_x.data_ptr(), out.data_ptr(), 0, count.data_ptr(), n, ka.KA_PRED_LT, 1 << 31, 0)
+        raw = np.frombuffer(items.tobytes(), dtype=np.uint8)
+        d_items = torch.from_numpy(raw.copy()).cuda()
+        ws = Workspace(ka, n, shape, batch_items=1)
+    else:
+        ws = Workspace(ka, n, shape)
+    if what == "scan":
+        want_out, want_count = oracle.exclusive_scan(x)
+    else:
+        want_out, want_count = oracle.compact(x, "lt", 1 << 31)
+
+    def launch():
+        if what == "compact":
+            return ka.ka_compact(d_x, n, None, ka.KA_PRED_LT, 1 << 31, 0, out, count, ws.ptr, ws.nbytes, shape,
+                                 stream())
+        if what == "scan":
+            return ka.ka_exclusive_scan(d_x, n, None, out, count, ws.ptr, ws.nbytes, shape, stream())
+        return ka.ka_compact_batch(d_items, 1, 1, ws.ptr, ws.nbytes, shape, 0, stream())
+
+    def check_result():
+        k = word(count)
+        assert k == want_count
+        assert np.array_equal(to_host(out, n if what == "scan" else k), want_out)
+
+    hdr = ws.header_words()
+    timed_out = False
+    for _ in range(32):
+        assert ka.ka_workspace_init(ws.ptr, ws.nbytes, stream()) == 0
+        assert ka.ka_workspace_set_spin_limit(ws.ptr, 64, stream()) == 0
+        torch.cuda.synchronize()
+        epoch = int(hdr[0].item()) >> 32
+        hdr[0] = (epoch << 32) | (G - 1)  # G - 1 tickets of this epoch already taken
+        assert launch() == 0
+        torch.cuda.synchronize()
+        st = ws.status(ka)
+        if st == ka.KA_E_DEVICE_TIMEOUT:
+            timed_out = True
+            break
+        assert st == 0
+        check_result()  # every block landed before the reset: one epoch, a normal launch
+    assert timed_out
+    # re-initialised, the same workspace works again
+    assert ka.ka_workspace_init(ws.ptr, ws.nbytes, stream()) == 0
+    out.fill_(int(np.uint32(SENTINEL).view(np.int32)))
+    assert launch() == 0
+    torch.cuda.synchronize()
+    assert ws.status(ka) == 0
+    check_result()
