@@ -13,9 +13,15 @@
 //                references are forwarded to the next stage's mailbox before
 //                the kernels finish (stream order replaces OpenCL events).
 //   * Request  - the promise of the composition: after the last stage the
-//                dispatcher records an event; a completion thread waits for it,
-//                reads the result length (and, in value mode, the data), and
-//                fulfils the request.
+//                dispatcher records an event. A receiver that is waiting polls
+//                that event itself; otherwise a completion thread waits for it.
+//                Whichever claims the request first reads the result length
+//                (and, in value mode, the data) and fulfils the promise.
+//   * Inline dispatch - a request whose first actor has no mail queued is
+//                dispatched on the requesting thread, under the same lock the
+//                dispatcher holds while it runs actors, so each actor still
+//                takes one message at a time and in mailbox order; the
+//                dispatcher thread carries the rest.
 // Memory: a dedicated CUDA memory pool with stream-ordered allocation on the
 // system stream, and a byte budget over the live references.
 #include <atomic>
@@ -194,6 +200,12 @@ struct Request {
     std::condition_variable cv;
     std::atomic<bool> done{false};
     bool debug_check = false;
+    // holders: the caller's handle, plus the completion queue once the last
+    // stage has been issued; the last holder frees the request
+    std::atomic<int> holders{1};
+    std::atomic<bool> recorded{false};  // event recorded after the last stage
+    std::atomic<bool> claimed{false};   // a thread has taken on fulfilling the promise
+    std::atomic<bool> waiting{false};   // a receiver is polling the event
 };
 
 struct Msg : QNode {
@@ -214,6 +226,7 @@ struct System {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t readback = nullptr;
+    std::mutex readback_mu;  // value-mode copies on `readback` (one claimer at a time)
     cudaMemPool_t pool = nullptr;
     uint64_t budget = 0;
     std::atomic<uint64_t> in_use{0};  // budget held: blocks handed out plus blocks in the cache
@@ -235,10 +248,15 @@ struct System {
     uint32_t *pinned = nullptr;
     std::vector<uint32_t> pin_free;
 
-    std::mutex ev_mu;
-    std::vector<cudaEvent_t> events;
+    // finished requests kept for reuse, each with its pinned count slot and
+    // completion event
+    std::mutex req_mu;
+    std::vector<Request *> req_free;
 
     MpscQueue runq;
+    // held while actors run (dispatcher or inline dispatch on a requesting
+    // thread): actors take one message at a time, launches stay in order
+    std::mutex dispatch_mu;
     std::mutex wake_mu;
     std::condition_variable wake_cv;
     std::atomic<bool> sleeping{false};
@@ -554,38 +572,24 @@ static ka_status run_stage(System *s, const StageSpec &sp, Msg *m, Ref **outs, i
     }
 }
 
-static cudaEvent_t take_event(System *s) {
-    std::lock_guard<std::mutex> l(s->ev_mu);
-    if (!s->events.empty()) {
-        cudaEvent_t e = s->events.back();
-        s->events.pop_back();
-        return e;
-    }
-    cudaEvent_t e = nullptr;
-    cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
-    return e;
-}
-
-static void give_event(System *s, cudaEvent_t e) {
-    std::lock_guard<std::mutex> l(s->ev_mu);
-    s->events.push_back(e);
-}
-
-static void process(System *s, Actor *a, Msg *m) {
+// Runs actor a on message m (the caller holds dispatch_mu). Returns the next
+// stage's actor, to which m is to be posted, or nullptr once m is consumed
+// (the request failed, or its last stage has been issued).
+static Actor *process(System *s, Actor *a, Msg *m) {
     Request *r = m->req;
     if (s->stop.load()) {
         fail_request(m, KA_E_CLOSED);
-        return;
+        return nullptr;
     }
     const int32_t fa = a->fail_after.load();
     const uint64_t seen = a->processed.fetch_add(1);
     if (fa >= 0 && seen >= uint64_t(fa)) {
         fail_request(m, KA_E_INJECTED);
-        return;
+        return nullptr;
     }
     if (m->n_refs != a->spec.in_arity) {
         fail_request(m, KA_E_TYPE);
-        return;
+        return nullptr;
     }
     Ref *outs[KA_MSG_MAX_REFS];
     int n_outs = 0;
@@ -593,7 +597,7 @@ static void process(System *s, Actor *a, Msg *m) {
     if (e != KA_OK) {
         for (int i = 0; i < n_outs; ++i) ref_drop(outs[i]);
         fail_request(m, e);
-        return;
+        return nullptr;
     }
     release_msg_refs(m);
     const int next = m->stage + 1;
@@ -601,8 +605,7 @@ static void process(System *s, Actor *a, Msg *m) {
         m->stage = next;
         m->n_refs = n_outs;
         for (int i = 0; i < n_outs; ++i) m->refs[i] = outs[i];
-        post(r->stages[next], m);
-        return;
+        return r->stages[next];
     }
     // Last stage: read the result length back and fulfil the promise once the
     // stream reaches this point.
@@ -618,14 +621,30 @@ static void process(System *s, Actor *a, Msg *m) {
     if (r->debug_check && s->ws)
         cudaMemcpyAsync(r->pinned_count + 1, &static_cast<WsHeader *>(s->ws)->error, 4, cudaMemcpyDeviceToHost,
                         s->stream);
-    r->event = take_event(s);
-    cudaEventRecord(r->event, s->stream);
+    cudaError_t rec = cudaSuccess;
+    if (!r->event) rec = cudaEventCreateWithFlags(&r->event, cudaEventDisableTiming);
+    if (rec == cudaSuccess) rec = cudaEventRecord(r->event, s->stream);
+    if (rec != cudaSuccess) {
+        cudaGetLastError();
+        r->claimed.store(true);
+        complete(r, cuda_status(rec));
+        return nullptr;
+    }
+    r->holders.fetch_add(1, std::memory_order_relaxed);  // the completion queue's hold
+    r->recorded.store(true, std::memory_order_release);
     {
         std::lock_guard<std::mutex> l(s->comp_mu);
         s->comp_q.push_back({r});
     }
     s->comp_pushed.fetch_add(1, std::memory_order_release);
     s->comp_cv.notify_one();
+    return nullptr;
+}
+
+// An actor with no mail queued and not waiting on the run queue: a message
+// dispatched to it now cannot overtake one sent to it earlier.
+static bool actor_idle(Actor *a) {
+    return !a->scheduled.load(std::memory_order_acquire) && !a->mailbox.maybe_nonempty();
 }
 
 static void fire_monitor(System *s, ka_status reason) {
@@ -682,16 +701,41 @@ static void dispatcher_main(System *s) {
         }
         idle_since = std::chrono::steady_clock::now();
         Actor *a = reinterpret_cast<Actor *>(reinterpret_cast<char *>(n) - offsetof(Actor, run_node));
-        for (int k = 0; k < 64; ++k) {
-            QNode *q = a->mailbox.pop();
-            if (!q) break;
-            process(s, a, static_cast<Msg *>(q));
+        {
+            std::lock_guard<std::mutex> dl(s->dispatch_mu);
+            for (int k = 0; k < 64; ++k) {
+                QNode *q = a->mailbox.pop();
+                if (!q) break;
+                Msg *m = static_cast<Msg *>(q);
+                if (Actor *nx = process(s, a, m)) post(nx, m);
+            }
+            a->scheduled.store(false, std::memory_order_release);
         }
-        a->scheduled.store(false, std::memory_order_release);
         if (a->mailbox.maybe_nonempty()) schedule(a);
     }
     drain_with(s, KA_E_CLOSED);
 }
+
+// Fulfils request r once its event has completed (status st of the wait):
+// result length, device error word, value-mode data. Run by the one thread
+// that claimed r.
+static void finalize(System *s, Request *r, ka_status st) {
+    r->count = r->pinned_count[0];
+    if (st == KA_OK && r->pinned_count[1] != 0) st = -int32_t(r->pinned_count[1]);
+    if (st == KA_OK && r->h_out && !r->result.empty()) {
+        Ref *y = r->result[0];
+        uint64_t k = r->count < r->h_out_cap ? r->count : r->h_out_cap;
+        if (k > y->capacity) k = y->capacity;
+        if (k) {
+            std::lock_guard<std::mutex> l(s->readback_mu);
+            st = cuda_status(cudaMemcpyAsync(r->h_out, y->ptr, k * 4, cudaMemcpyDeviceToHost, s->readback));
+            if (st == KA_OK) st = cuda_status(cudaStreamSynchronize(s->readback));
+        }
+    }
+    complete(r, st);
+}
+
+static void request_unhold(Request *r);
 
 static void completer_main(System *s) {
     cudaSetDevice(s->device);
@@ -714,21 +758,15 @@ static void completer_main(System *s) {
             ++taken;
         }
         Request *r = c.req;
-        ka_status st = cuda_status(cudaEventSynchronize(r->event));
-        give_event(s, r->event);
-        r->event = nullptr;
-        r->count = r->pinned_count[0];
-        if (st == KA_OK && r->pinned_count[1] != 0) st = -int32_t(r->pinned_count[1]);
-        if (st == KA_OK && r->h_out && !r->result.empty()) {
-            Ref *y = r->result[0];
-            uint64_t k = r->count < r->h_out_cap ? r->count : r->h_out_cap;
-            if (k > y->capacity) k = y->capacity;
-            if (k) {
-                st = cuda_status(cudaMemcpyAsync(r->h_out, y->ptr, k * 4, cudaMemcpyDeviceToHost, s->readback));
-                if (st == KA_OK) st = cuda_status(cudaStreamSynchronize(s->readback));
-            }
+        // A receiver polling r fulfils it itself; this thread stays out of the
+        // driver meanwhile and steps in only once no receiver is polling.
+        while (!r->claimed.load(std::memory_order_acquire) && r->waiting.load(std::memory_order_acquire))
+            std::this_thread::yield();
+        if (!r->claimed.load(std::memory_order_acquire)) {
+            const ka_status st = cuda_status(cudaEventSynchronize(r->event));
+            if (!r->claimed.exchange(true, std::memory_order_acq_rel)) finalize(s, r, st);
         }
-        complete(r, st);
+        request_unhold(r);
     }
 }
 
@@ -753,16 +791,51 @@ static uint32_t *take_pinned(System *s) {
     return s->pinned + 2 * i;
 }
 
-static void give_pinned(System *s, uint32_t *p) {
-    std::lock_guard<std::mutex> l(s->pin_mu);
-    s->pin_free.push_back(uint32_t((p - s->pinned) / 2));
+// A request object: a recycled one when the system has one, else a new one
+// with its own pinned count slot (nullptr when the slots are used up).
+static Request *request_new(System *s) {
+    {
+        std::lock_guard<std::mutex> l(s->req_mu);
+        if (!s->req_free.empty()) {
+            Request *r = s->req_free.back();
+            s->req_free.pop_back();
+            return r;
+        }
+    }
+    uint32_t *pin = take_pinned(s);
+    if (!pin) return nullptr;
+    Request *r = new Request;
+    r->sys = s;
+    r->pinned_count = pin;
+    return r;
 }
 
-static void request_free(Request *r) {
+// Returns an unused request (no handle, no stages, no result) for reuse.
+static void request_recycle(Request *r) {
+    r->handle = 0;
+    r->h_out = nullptr;
+    r->h_out_cap = 0;
+    r->count = 0;
+    r->status = KA_OK;
+    r->debug_check = false;
+    r->done.store(false, std::memory_order_relaxed);
+    r->holders.store(1, std::memory_order_relaxed);
+    r->recorded.store(false, std::memory_order_relaxed);
+    r->claimed.store(false, std::memory_order_relaxed);
+    r->waiting.store(false, std::memory_order_relaxed);
+    System *s = r->sys;
+    std::lock_guard<std::mutex> l(s->req_mu);
+    s->req_free.push_back(r);
+}
+
+// Drops one holder of r; the last one releases what it holds and recycles it.
+static void request_unhold(Request *r) {
+    if (r->holders.fetch_sub(1, std::memory_order_acq_rel) != 1) return;
     for (Ref *x : r->result) ref_drop(x);
+    r->result.clear();
     for (Actor *a : r->stages) actor_drop(a);
-    if (r->pinned_count) give_pinned(r->sys, r->pinned_count);
-    delete r;
+    r->stages.clear();
+    request_recycle(r);
 }
 
 }  // namespace rt
@@ -851,7 +924,10 @@ ka_status ka_system_destroy(ka_system *h, int32_t force) {
     cache_flush(s);
     if (s->ws) cudaFreeAsync(s->ws, s->stream);
     cudaStreamSynchronize(s->stream);
-    for (cudaEvent_t e : s->events) cudaEventDestroy(e);
+    for (Request *r : s->req_free) {
+        if (r->event) cudaEventDestroy(r->event);
+        delete r;
+    }
     if (s->pinned) cudaFreeHost(s->pinned);
     cudaStreamDestroy(s->readback);
     if (s->own_stream) cudaStreamDestroy(s->stream);
@@ -1107,18 +1183,15 @@ ka_status ka_request(ka_actor *h, const ka_msg *in, ka_request_h **out) {
             m->refs[m->n_refs++] = r;
         }
     }
-    Request *r = new Request;
-    r->sys = s;
+    Request *r = request_new(s);
+    if (!r) {
+        release_msg_refs(m);
+        delete m;
+        return KA_E_OOM;
+    }
     r->h_out = in->h_out;
     r->h_out_cap = in->h_out_cap;
     r->debug_check = s->debug;
-    r->pinned_count = take_pinned(s);
-    if (!r->pinned_count) {
-        release_msg_refs(m);
-        delete m;
-        delete r;
-        return KA_E_OOM;
-    }
     // value mode in: the first stage's input is uploaded from host memory
     if (in->h_in) {
         if (m->n_refs > 0) {
@@ -1139,8 +1212,7 @@ ka_status ka_request(ka_actor *h, const ka_msg *in, ka_request_h **out) {
             m->refs[0] = nullptr;
             for (int j = 1; j < m->n_refs; ++j) ref_drop(m->refs[j]);
             delete m;
-            give_pinned(s, r->pinned_count);
-            delete r;
+            request_recycle(r);
             return st;
         }
         m->refs[0] = u;
@@ -1153,20 +1225,37 @@ ka_status ka_request(ka_actor *h, const ka_msg *in, ka_request_h **out) {
     m->stage = 0;
     r->handle = g_requests.add(r);
     s->inflight.fetch_add(1);
-    post(r->stages[0], m);
     *out = reinterpret_cast<ka_request_h *>(r->handle);
+    // Inline dispatch: while no thread runs actors and the next actor has no
+    // mail queued, run the stages here; the rest goes through the mailboxes.
+    Actor *a = r->stages[0];
+    if (!s->kill_requested.load() && s->dispatch_mu.try_lock()) {
+        while (a && actor_idle(a)) a = process(s, a, m);
+        s->dispatch_mu.unlock();
+    }
+    if (a) post(a, m);
     return KA_OK;
 }
 
 ka_status ka_receive(ka_request_h *h, int64_t timeout_ns, ka_msg *out) {
     Request *r = g_requests.get(reinterpret_cast<uint64_t>(h));
     if (!r) return KA_E_STALE;
-    // spin for a while (no wake-up latency for results that come soon), then block
+    // Spin for a while (no wake-up latency for results that come soon),
+    // polling the request's event once it is recorded and fulfilling the
+    // request on this thread if it claims it first; then block.
     if (!r->done.load(std::memory_order_acquire)) {
+        System *s = r->sys;
+        r->waiting.store(true, std::memory_order_release);
         const auto t0 = std::chrono::steady_clock::now();
         const auto spin = std::chrono::microseconds(kReceiveSpinUs);
         while (!r->done.load(std::memory_order_acquire) && std::chrono::steady_clock::now() - t0 < spin) {
+            if (!r->recorded.load(std::memory_order_acquire) || r->claimed.load(std::memory_order_acquire)) continue;
+            const cudaError_t q = cudaEventQuery(r->event);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) cudaGetLastError();
+            if (!r->claimed.exchange(true, std::memory_order_acq_rel)) finalize(s, r, cuda_status(q));
         }
+        r->waiting.store(false, std::memory_order_release);
         if (!r->done.load(std::memory_order_acquire)) {
             std::unique_lock<std::mutex> l(r->mu);
             if (timeout_ns < 0) {
@@ -1194,7 +1283,7 @@ ka_status ka_receive(ka_request_h *h, int64_t timeout_ns, ka_msg *out) {
             r->result.clear();
         }
     }
-    request_free(r);
+    request_unhold(r);
     return st;
 }
 
