@@ -344,3 +344,100 @@ def test_concurrent_requesters(ka, system):
         t.join()
     assert not errors, errors
     ka.ka_actor_release(comp)
+
+
+def three_actor(ka, sys_h, mask):
+    pred = spawn(ka, sys_h, ka.KA_STAGE_PREDICATE, ka.KA_PRED_AND_MASK_EQ0, mask)
+    scan = spawn(ka, sys_h, ka.KA_STAGE_EXSCAN)
+    scat = spawn(ka, sys_h, ka.KA_STAGE_SCATTER)
+    return compose(ka, scat, scan, pred), (pred, scan, scat)
+
+
+def test_results_received_in_reverse_order(ka, system):
+    """Requests that finish while nobody waits on them are fulfilled by the
+    completion thread; receiving them later, in reverse order, gives each its
+    own result."""
+    pipe, parts = three_actor(ka, system, 3)
+    inputs, reqs = [], []
+    for i in range(16):
+        x = ki.uniform_u32(100 + i, 3000 + 4099 * i)
+        d_x = to_dev(x)
+        s, rx = ka.ka_ref_wrap(system, d_x, x.size, x.size)
+        assert s == 0
+        s, q = ka.ka_request(pipe, ka.make_msg([rx]))
+        assert s == 0
+        inputs.append((x, d_x, rx))
+        reqs.append(q)
+    torch.cuda.synchronize()
+    for (x, _, rx), q in reversed(list(zip(inputs, reqs))):
+        s, m = ka.ka_receive(q)
+        assert s == 0
+        y, k = oracle.compact(x, "and_mask_eq0", 3)
+        assert m.count == k and np.array_equal(result_data(ka, m.refs[0], k), y)
+        for j in range(m.n_refs):
+            ka.ka_ref_release(m.refs[j])
+        ka.ka_ref_release(rx)
+    assert ka.ka_system_pool_bytes(system)[1] == 0
+    for a in (pipe,) + parts:
+        ka.ka_actor_release(a)
+
+
+def test_threads_share_composite_with_device_refs(ka, system):
+    """Four threads drive one composite over device references: requests run
+    on the requesting thread while its actors are idle and through the
+    mailboxes and the dispatcher thread otherwise; every result matches the
+    oracle and the pool is empty afterwards."""
+    pipe, parts = three_actor(ka, system, 1)
+    cases = []
+    for t in range(4):
+        for i in range(12):
+            x = ki.uniform_u32(7000 + 100 * t + i, 1 + 2749 * (t * 12 + i))
+            cases.append((t, x, to_dev(x)))
+    torch.cuda.synchronize()
+    errors = []
+
+    def worker(tid):
+        try:
+            for t, x, d_x in cases:
+                if t != tid:
+                    continue
+                s, rx = ka.ka_ref_wrap(system, d_x, x.size, x.size)
+                assert s == 0
+                s, q = ka.ka_request(pipe, ka.make_msg([rx]))
+                assert s == 0
+                s, m = ka.ka_receive(q)
+                assert s == 0
+                y, k = oracle.compact(x, "and_mask_eq0", 1)
+                assert m.count == k and np.array_equal(result_data(ka, m.refs[0], k), y)
+                for j in range(m.n_refs):
+                    ka.ka_ref_release(m.refs[j])
+                ka.ka_ref_release(rx)
+        except Exception as e:  # pragma: no cover - reported below
+            errors.append(repr(e))
+
+    ts = [threading.Thread(target=worker, args=(t,)) for t in range(4)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errors, errors
+    assert ka.ka_system_pool_bytes(system)[1] == 0
+    for a in (pipe,) + parts:
+        ka.ka_actor_release(a)
+
+
+def test_receiver_that_blocks_gets_result(ka, system):
+    """A request that outlasts the receiver's spin window (a Mandelbrot stage
+    of 8192 x 4096 pixels, up to 2000 steps each) is fulfilled by the
+    completion thread and wakes the blocked receiver."""
+    w, h, iters = 8192, 4096, 2000
+    a = spawn(ka, system, ka.KA_STAGE_MANDELBROT, w, iters, h)
+    for _ in range(2):
+        s, q = ka.ka_request(a, ka.make_msg())
+        assert s == 0
+        s, m = ka.ka_receive(q)
+        assert s == 0 and m.count == w * h
+        for j in range(m.n_refs):
+            ka.ka_ref_release(m.refs[j])
+    assert ka.ka_system_pool_bytes(system)[1] == 0
+    ka.ka_actor_release(a)
