@@ -83,8 +83,9 @@ ka_status ka_bench_direct_chain(const ka_stage_desc *stages, uint32_t n_stages, 
     if (cudaMalloc(&ws, ws_bytes) != cudaSuccess) return KA_E_OOM;
     allocs.push_back(ws);
     s = ka_workspace_init(ws, ws_bytes, st);
-    uint32_t *pinned = nullptr;
-    if (s == KA_OK) s = cuda_status(cudaHostAlloc(&pinned, 16, cudaHostAllocDefault));
+    uint32_t *pinned = nullptr, *pinned_dev = nullptr;  // host-mapped result word, as the actor layer uses
+    if (s == KA_OK) s = cuda_status(cudaHostAlloc(&pinned, 16, cudaHostAllocMapped));
+    if (s == KA_OK) s = cuda_status(cudaHostGetDevicePointer(reinterpret_cast<void **>(&pinned_dev), pinned, 0));
     // plan: per stage, its outputs (same arity conventions as the actor stages)
     std::vector<std::vector<Buf>> outs(n_stages);
     std::vector<Buf> cur;
@@ -183,9 +184,9 @@ ka_status ka_bench_direct_chain(const ka_stage_desc *stages, uint32_t n_stages, 
             if (e != KA_OK) return e;
             c = o;
         }
-        // the result length comes back to the host, as a receive would deliver it
+        // the result length comes back to the host the way a receive delivers it
         if (c[0].count) {
-            ka_status e = cuda_status(cudaMemcpyAsync(pinned, c[0].count, 4, cudaMemcpyDeviceToHost, st));
+            ka_status e = launch_publish(c[0].count, 1, 0, nullptr, pinned_dev, nullptr, st);
             if (e != KA_OK) return e;
         } else {
             pinned[0] = uint32_t(c[0].n);

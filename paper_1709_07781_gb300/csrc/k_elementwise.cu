@@ -163,6 +163,30 @@ ka_status launch_copy_count(const uint32_t *n_ptr, uint64_t n, uint32_t *n_out, 
     return cuda_status(cudaGetLastError());
 }
 
+// Result publication: n words from device memory (or, with src null, the
+// value `fixed` as one word) and, when err is given, the device error word,
+// stored straight into host-mapped pinned memory. One small launch stands in
+// for device-to-host copies, whose copy-engine round trip costs several
+// microseconds even for a single word.
+__global__ void k_publish(const uint32_t *src, uint32_t n, uint32_t fixed, const uint32_t *err, uint32_t *dst,
+                          uint32_t *dst_err) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (!src) {
+        if (t == 0) dst[0] = fixed;
+    } else {
+        for (uint32_t i = t; i < n; i += blockDim.x * gridDim.x) dst[i] = src[i];
+    }
+    if (err && t == 0) *dst_err = *err;
+}
+
+ka_status launch_publish(const uint32_t *src, uint32_t n, uint32_t fixed, const uint32_t *err, uint32_t *dst,
+                         uint32_t *dst_err, cudaStream_t stream) {
+    if (!dst || (err && !dst_err)) return KA_E_ARG;
+    const uint32_t blocks = src && n > 256 ? std::min<uint32_t>((n + 255) / 256, 16u) : 1u;
+    k_publish<<<blocks, 256, 0, stream>>>(src, n, fixed, err, dst, dst_err);
+    return cuda_status(cudaGetLastError());
+}
+
 // The empty stage: one launch that does no work (prices a message-passing stage).
 __global__ void k_empty() {}
 

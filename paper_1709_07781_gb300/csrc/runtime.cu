@@ -194,7 +194,8 @@ struct Request {
     std::vector<Ref *> result;
     uint64_t count = 0;
     ka_status status = KA_OK;
-    uint32_t *pinned_count = nullptr;
+    uint32_t *pinned_count = nullptr;  // host-mapped slot: length, device error word
+    uint32_t *pinned_dev = nullptr;    // the same slot as the device addresses it
     cudaEvent_t event = nullptr;
     std::mutex mu;
     std::condition_variable cv;
@@ -246,6 +247,7 @@ struct System {
     // pinned slots for result counts
     std::mutex pin_mu;
     uint32_t *pinned = nullptr;
+    uint32_t *pinned_dev = nullptr;  // device address of `pinned` (host-mapped)
     std::vector<uint32_t> pin_free;
 
     // finished requests kept for reuse, each with its pinned count slot and
@@ -611,23 +613,23 @@ static Actor *process(System *s, Actor *a, Msg *m) {
     // stream reaches this point.
     delete m;
     r->result.assign(outs, outs + n_outs);
+    // The length (and in debug mode the device error word) is stored into the
+    // request's host-mapped slot by a one-thread kernel on the stream.
     Ref *first = n_outs ? outs[0] : nullptr;
-    if (first && first->d_count) {
-        cudaMemcpyAsync(r->pinned_count, first->d_count, 4, cudaMemcpyDeviceToHost, s->stream);
-    } else if (first) {
-        *r->pinned_count = uint32_t(first->n_host);
-    }
+    const uint32_t *err = r->debug_check && s->ws ? &static_cast<WsHeader *>(s->ws)->error : nullptr;
+    r->pinned_count[0] = first && !first->d_count ? uint32_t(first->n_host) : 0u;
     r->pinned_count[1] = 0;
-    if (r->debug_check && s->ws)
-        cudaMemcpyAsync(r->pinned_count + 1, &static_cast<WsHeader *>(s->ws)->error, 4, cudaMemcpyDeviceToHost,
-                        s->stream);
+    ka_status pub = KA_OK;
+    if ((first && first->d_count) || err)
+        pub = launch_publish(first ? first->d_count : nullptr, 1, r->pinned_count[0], err, r->pinned_dev,
+                             r->pinned_dev + 1, s->stream);
     cudaError_t rec = cudaSuccess;
-    if (!r->event) rec = cudaEventCreateWithFlags(&r->event, cudaEventDisableTiming);
-    if (rec == cudaSuccess) rec = cudaEventRecord(r->event, s->stream);
-    if (rec != cudaSuccess) {
-        cudaGetLastError();
+    if (pub == KA_OK && !r->event) rec = cudaEventCreateWithFlags(&r->event, cudaEventDisableTiming);
+    if (pub == KA_OK && rec == cudaSuccess) rec = cudaEventRecord(r->event, s->stream);
+    if (pub != KA_OK || rec != cudaSuccess) {
+        if (rec != cudaSuccess) cudaGetLastError();
         r->claimed.store(true);
-        complete(r, cuda_status(rec));
+        complete(r, pub != KA_OK ? pub : cuda_status(rec));
         return nullptr;
     }
     r->holders.fetch_add(1, std::memory_order_relaxed);  // the completion queue's hold
@@ -807,6 +809,7 @@ static Request *request_new(System *s) {
     Request *r = new Request;
     r->sys = s;
     r->pinned_count = pin;
+    r->pinned_dev = s->pinned_dev + (pin - s->pinned);
     return r;
 }
 
@@ -885,8 +888,11 @@ ka_status ka_system_create(const ka_config *cfg, ka_system **out) {
             cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
         }
     }
-    if (st == KA_OK) st = cuda_status(cudaHostAlloc(&s->pinned, size_t(kPinnedSlots) * 8, cudaHostAllocDefault));
+    if (st == KA_OK) st = cuda_status(cudaHostAlloc(&s->pinned, size_t(kPinnedSlots) * 8, cudaHostAllocMapped));
+    if (st == KA_OK)
+        st = cuda_status(cudaHostGetDevicePointer(reinterpret_cast<void **>(&s->pinned_dev), s->pinned, 0));
     if (st != KA_OK) {
+        if (s->pinned) cudaFreeHost(s->pinned);
         if (s->readback) cudaStreamDestroy(s->readback);
         if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
         if (s->pool) cudaMemPoolDestroy(s->pool);

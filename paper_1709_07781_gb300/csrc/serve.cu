@@ -49,7 +49,8 @@ uint64_t bytes_for(uint32_t n) { return n ? (uint64_t(n) * 4 + 255) / 256 * 256 
 
 struct Tick {
     char *dev = nullptr;   // gen items | stage tables | counts | error word
-    char *host = nullptr;  // pinned mirror of the same layout
+    char *host = nullptr;      // pinned, host-mapped mirror of the same layout
+    char *host_dev = nullptr;  // the mirror's device address
     cudaEvent_t ev = nullptr;
     std::vector<uint32_t> reqs;  // request indices, tick position = vector index
     uint32_t depth = 0;          // stages of the deepest request
@@ -119,7 +120,8 @@ struct Run {
     std::deque<Slot> plain_inflight;
     std::vector<uint32_t> plain_free;
     uint32_t *d_cnt = nullptr;  // kDepth words per slot
-    uint32_t *h_cnt = nullptr;  // final count per slot
+    uint32_t *h_cnt = nullptr;      // final count per slot (host-mapped)
+    uint32_t *h_cnt_dev = nullptr;  // its device address
     std::vector<cudaEvent_t> plain_ev;
     void *ws_plain = nullptr;
     uint64_t ws_plain_bytes = 0;
@@ -189,6 +191,13 @@ bool admit_head(Run &R, uint32_t *out) {
 }
 
 // ----------------------------------------------------------------- batched mode
+// The tick's per-stage counts and the batch workspace's error word, stored
+// into the tick's host-mapped mirror by one small launch.
+ka_status publish_counts(Run &R, Tick &T, uint32_t depth) {
+    return launch_publish(T.cnt(T.dev, 0), kTickItems * depth, 0, &static_cast<WsHeader *>(R.ws_cmp)->error,
+                          T.cnt(T.host_dev, 0), T.err(T.host_dev), R.stream);
+}
+
 ka_status issue_tick(Run &R, bool *issued) {
     *issued = false;
     if (R.tick_used == kTicks || R.waiting.empty()) return KA_OK;
@@ -261,12 +270,10 @@ ka_status issue_tick(Run &R, bool *issued) {
                              &R.batch_tile, grid, st);
         R.st.launches += 2;
     }
-    if (s == KA_OK)
-        s = cuda_status(cudaMemcpyAsync(T.cnt(T.host, 0), T.cnt(T.dev, 0), sizeof(uint32_t) * kTickItems * T.depth,
-                                        cudaMemcpyDeviceToHost, st));
-    if (s == KA_OK)
-        s = cuda_status(cudaMemcpyAsync(T.err(T.host), &static_cast<WsHeader *>(R.ws_cmp)->error, 4,
-                                        cudaMemcpyDeviceToHost, st));
+    if (s == KA_OK) {
+        s = publish_counts(R, T, T.depth);
+        R.st.launches += 1;
+    }
     if (s == KA_OK) s = cuda_status(cudaEventRecord(T.ev, st));
     if (s != KA_OK) return s;
     T.busy = true;
@@ -290,12 +297,7 @@ ka_status full_tick_ops(Run &R, Tick &T, uint32_t depth) {
     for (uint32_t d = 0; d < depth && s == KA_OK; ++d)
         s = ka_compact_batch(T.items(T.dev, int(d)), kTickItems, kTickItems, R.ws_cmp, R.ws_cmp_bytes, &R.batch_tile,
                              0, st);
-    if (s == KA_OK)
-        s = cuda_status(cudaMemcpyAsync(T.cnt(T.host, 0), T.cnt(T.dev, 0), sizeof(uint32_t) * kTickItems * depth,
-                                        cudaMemcpyDeviceToHost, st));
-    if (s == KA_OK)
-        s = cuda_status(cudaMemcpyAsync(T.err(T.host), &static_cast<WsHeader *>(R.ws_cmp)->error, 4,
-                                        cudaMemcpyDeviceToHost, st));
+    if (s == KA_OK) s = publish_counts(R, T, depth);
     return s;
 }
 
@@ -384,8 +386,7 @@ ka_status issue_plain(Run &R, bool *issued) {
             R.st.launches += 1;
         }
         if (s == KA_OK)
-            s = cuda_status(cudaMemcpyAsync(R.h_cnt + slot, cnt + q.n_stages - 1, 4, cudaMemcpyDeviceToHost,
-                                            R.stream));
+            s = launch_publish(cnt + q.n_stages - 1, 1, 0, nullptr, R.h_cnt_dev + slot, nullptr, R.stream);
         if (s == KA_OK) s = cuda_status(cudaEventRecord(R.plain_ev[slot], R.stream));
         if (s != KA_OK) return s;
         R.plain_inflight.push_back(Run::Slot{r, R.plain_ev[slot], slot});
@@ -438,7 +439,10 @@ ka_status setup(Run &R, uint32_t max_n) {
         if (s == KA_OK) s = ka_workspace_init(R.ws_cmp, R.ws_cmp_bytes, R.stream);
         for (int i = 0; i < kTicks && s == KA_OK; ++i) {
             s = cuda_status(cudaMalloc(&R.ticks[i].dev, Tick::kBytes));
-            if (s == KA_OK) s = cuda_status(cudaHostAlloc(&R.ticks[i].host, Tick::kBytes, cudaHostAllocDefault));
+            if (s == KA_OK) s = cuda_status(cudaHostAlloc(&R.ticks[i].host, Tick::kBytes, cudaHostAllocMapped));
+            if (s == KA_OK)
+                s = cuda_status(
+                    cudaHostGetDevicePointer(reinterpret_cast<void **>(&R.ticks[i].host_dev), R.ticks[i].host, 0));
             if (s == KA_OK) s = cuda_status(cudaEventCreateWithFlags(&R.ticks[i].ev, cudaEventDisableTiming));
             if (s == KA_OK) s = cuda_status(cudaMemsetAsync(R.ticks[i].dev, 0, Tick::kBytes, R.stream));
             if (s == KA_OK) std::memset(R.ticks[i].host, 0, Tick::kBytes);  // zero entries are empty items
@@ -450,7 +454,8 @@ ka_status setup(Run &R, uint32_t max_n) {
         if (s == KA_OK) s = cuda_status(cudaMalloc(&R.ws_plain, R.ws_plain_bytes));
         if (s == KA_OK) s = ka_workspace_init(R.ws_plain, R.ws_plain_bytes, R.stream);
         if (s == KA_OK) s = cuda_status(cudaMalloc(&R.d_cnt, sizeof(uint32_t) * kDepth * slots));
-        if (s == KA_OK) s = cuda_status(cudaHostAlloc(&R.h_cnt, sizeof(uint32_t) * slots, cudaHostAllocDefault));
+        if (s == KA_OK) s = cuda_status(cudaHostAlloc(&R.h_cnt, sizeof(uint32_t) * slots, cudaHostAllocMapped));
+        if (s == KA_OK) s = cuda_status(cudaHostGetDevicePointer(reinterpret_cast<void **>(&R.h_cnt_dev), R.h_cnt, 0));
         R.plain_ev.assign(slots, nullptr);
         for (uint32_t i = 0; i < slots && s == KA_OK; ++i) {
             s = cuda_status(cudaEventCreateWithFlags(&R.plain_ev[i], cudaEventDisableTiming));
