@@ -10,8 +10,10 @@ needed between steps). Prints one JSON line.
              CUDA events on the launching stream, max over ranks)
   roofline   the fused kernel's algorithmic bytes (4 N + 4 K per launch) over
              its average launch time, against the measured HBM copy bandwidth
-  e2e        the same metric through the C ABI with host buffers: the step's
-             input uploaded from pinned memory, its results read back
+  e2e        the same metric through the C ABI with host buffers
+             (ka_compact_host): the step's input streamed from pinned memory
+             in 64 MiB chunks, every chunk's kept entries read back, the
+             transfers in both directions overlapped with the compactions
   cpu_baseline  the CPU oracle (plain sequential loop) on the host cores
 
 --impl reference times the CPU oracle as the reference arm on the same
@@ -327,36 +329,31 @@ def run_ours(args):
 
 
 def e2e_large(ka, torch, x_dev, kept, thresholds, ws, ws_bytes, D, steps):
-    """Whole step through the C ABI with host buffers: pinned input uploaded,
-    three compactions, counts and kept entries read back."""
+    """Whole step through the C ABI with host buffers: ka_compact_host streams
+    the pinned input to the device in 64 MiB chunks, compacts every chunk for
+    the three thresholds and reads each chunk's kept entries back into pinned
+    host buffers, with uploads, compactions and read-backs overlapped."""
     import numpy as np
     N = x_dev.numel()
-    st = torch.cuda.current_stream()
     h_x = torch.empty(N, dtype=torch.int32, pin_memory=True)
     h_x.copy_(x_dev.cpu())
     h_out = [torch.empty(N, dtype=torch.int32, pin_memory=True) for _ in range(3)]
-    h_cnt = torch.zeros(4, dtype=torch.int32, pin_memory=True)
-    d_x = torch.empty_like(x_dev)
-    d_out = [torch.empty_like(x_dev) for _ in range(3)]
-    d_cnt = torch.zeros(4, dtype=torch.int32, device=x_dev.device)
+    chunk = 1 << 24
+    s, nbytes = ka.ka_compact_host_scratch_size(chunk, 3)
+    ka.check(s)
+    scratch = torch.empty(nbytes + 256, dtype=torch.uint8, device=x_dev.device)
+    base = (scratch.data_ptr() + 255) // 256 * 256
+    lt = ka.PRED["lt"]
     h2d = d2h = 0
 
     def step():
         nonlocal h2d, d2h
-        d_x.copy_(h_x, non_blocking=True)
-        for i in range(3):
-            ka.check(ka.ka_compact(d_x, N, None, ka.KA_PRED_LT, thresholds[i], 0, d_out[i], d_cnt[i:i + 1], ws,
-                                   ws_bytes, None, st.cuda_stream))
-        h_cnt.copy_(d_cnt, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-        for i in range(3):
-            k = int(np.int32(h_cnt[i].item()).view(np.uint32))
-            if k:
-                h_out[i][:k].copy_(d_out[i][:k], non_blocking=True)
-            d2h += 4 * k
-        torch.cuda.current_stream().synchronize()
+        s, counts = ka.ka_compact_host(h_x, N, [lt] * 3, list(thresholds), [0, 0, 0], h_out, chunk, base, nbytes)
+        ka.check(s)
+        if counts != [int(k) for k in kept]:
+            raise RuntimeError("end-to-end counts %s differ from the device run %s" % (counts, kept))
         h2d += 4 * N
-        d2h += 16
+        d2h += 4 * sum(counts) + 4 * 3 * ((N + chunk - 1) // chunk)  # kept entries + per-chunk counts
 
     step()
     h2d = d2h = 0
@@ -367,9 +364,10 @@ def e2e_large(ka, torch, x_dev, kept, thresholds, ws, ws_bytes, D, steps):
     dt = time.perf_counter() - t0
     D.barrier()
     dt = D.max(dt)
+    del scratch
     return {"value": aggregate(3.0 * N * steps, D.world, dt), "unit": "elements/s",
             "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps, "steps": steps,
-            "ms_per_step": dt * 1000.0 / steps}
+            "ms_per_step": dt * 1000.0 / steps, "path": "ka_compact_host, 64 MiB chunks, pinned host buffers"}
 
 
 def three_launch_large(ka, torch, x, thresholds, D, peak):

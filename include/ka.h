@@ -201,6 +201,34 @@ ka_status ka_compact_three_phase(const uint32_t *d_in, uint64_t n, const uint32_
                                  uint32_t param, uint32_t xform, uint32_t *d_out, uint32_t *d_count,
                                  void *d_ws, uint64_t ws_bytes, void *stream);
 
+/* Compaction of a host array, streamed (the value mode of Sec. 3.5, where the
+ * first actor uploads the data and the last reads the result back; the paper
+ * has no streamed form). h_in[0..n) is uploaded in chunks of `chunk` entries
+ * (0: 2^24), each chunk is compacted on the device once per predicate
+ * p < n_pred (pred[p], param[p], xform[p] as for ka_compact), and the kept
+ * entries of each chunk are copied back into h_out[p], after those of the
+ * earlier chunks, as soon as the chunk's counts are known. Uploads of later
+ * chunks, compactions and read-backs of earlier chunks overlap. On KA_OK,
+ * count[p] is the number of kept entries and h_out[p][0..count[p]) holds them
+ * in input order; h_out[p] needs room for n entries. n may exceed 2^32.
+ * h_in and h_out[p] should be pinned (cudaHostAlloc or cudaHostRegister) for
+ * the transfers to overlap; pageable memory gives the same result, slower.
+ * d_scratch: ka_compact_host_scratch_size(chunk, n_pred) bytes of device
+ * memory, 256-byte aligned, owned by the caller, needing no initialisation,
+ * not used by anything else during the call. The call uses the current device
+ * and streams of its own, serialises with other calls on that device, and
+ * returns when the results are in host memory (every upload, kernel and copy
+ * it issued has finished, also on error). Errors: KA_E_ARG (n_pred of 0 or
+ * above KA_HOST_MAX_PRED, null pointers, chunk above 2^32 - 4, unaligned
+ * scratch), KA_E_WORKSPACE (scratch too small), a predicate's error,
+ * KA_E_CUDA, or a device status of the compaction (then h_out and count are
+ * undefined). */
+#define KA_HOST_MAX_PRED 4
+ka_status ka_compact_host_scratch_size(uint64_t chunk, uint32_t n_pred, uint64_t *bytes);
+ka_status ka_compact_host(const uint32_t *h_in, uint64_t n, uint32_t n_pred, const int32_t *pred,
+                          const uint32_t *param, const uint32_t *xform, uint32_t *const *h_out, uint64_t *count,
+                          uint64_t chunk, void *d_scratch, uint64_t scratch_bytes);
+
 /* Escape-time Mandelbrot image, the paper's compute workload (Sec. 5.4):
  * d_out[y * width + x] = number of steps z <- z^2 + c taken from z = 0 while
  * |z|^2 <= 4, at most max_iter, for c = (re_min + x dre, im_min + y dim),

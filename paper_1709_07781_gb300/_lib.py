@@ -131,6 +131,12 @@ _SIGS = {
     "ka_three_phase_workspace_size": (ctypes.c_int32, [ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
     "ka_compact_three_phase": (ctypes.c_int32, [c_vp, ctypes.c_uint64, c_vp, ctypes.c_int32, ctypes.c_uint32,
                                                 ctypes.c_uint32, c_vp, c_vp, c_vp, ctypes.c_uint64, c_vp]),
+    "ka_compact_host_scratch_size": (ctypes.c_int32, [ctypes.c_uint64, ctypes.c_uint32,
+                                                      ctypes.POINTER(ctypes.c_uint64)]),
+    "ka_compact_host": (ctypes.c_int32, [c_vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
+                                         ctypes.POINTER(c_vp), ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint64,
+                                         c_vp, ctypes.c_uint64]),
     "ka_mandelbrot": (ctypes.c_int32, [c_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_float, ctypes.c_float,
                                        ctypes.c_float, ctypes.c_float, ctypes.c_uint32, c_vp]),
     "ka_prepare_index": (ctypes.c_int32, [c_vp, c_vp, ctypes.c_uint64, c_vp, c_vp, c_vp, c_vp]),
@@ -293,6 +299,28 @@ def ka_compact_three_phase(d_in, n: int, d_n, pred: int, param: int, xform: int,
                            ws_bytes: int, stream=None) -> int:
     return lib.ka_compact_three_phase(ptr(d_in), n, ptr(d_n), pred, param, xform, ptr(d_out), ptr(d_count),
                                       ptr(d_ws), ws_bytes, stream_ptr(stream))
+
+
+KA_HOST_MAX_PRED = 4
+
+
+def ka_compact_host_scratch_size(chunk: int, n_pred: int):
+    out = ctypes.c_uint64(0)
+    s = lib.ka_compact_host_scratch_size(chunk, n_pred, ctypes.byref(out))
+    return s, out.value
+
+
+def ka_compact_host(h_in, n: int, preds, params, xforms, h_outs, chunk: int, d_scratch, scratch_bytes: int):
+    """Streamed compaction of host memory for len(preds) predicates; returns
+    (status, [count per predicate])."""
+    k = len(preds)
+    pa = (ctypes.c_int32 * k)(*preds)
+    qa = (ctypes.c_uint32 * k)(*params)
+    xa = (ctypes.c_uint32 * k)(*xforms)
+    oa = (c_vp * k)(*[ptr(o) for o in h_outs])
+    ca = (ctypes.c_uint64 * k)()
+    s = lib.ka_compact_host(ptr(h_in), n, k, pa, qa, xa, oa, ca, chunk, ptr(d_scratch), scratch_bytes)
+    return s, [int(c) for c in ca]
 
 
 def ka_mandelbrot(d_out, width: int, height: int, re_min: float, im_min: float, re_max: float, im_max: float,
