@@ -712,7 +712,9 @@ def serve_large(ka, torch):
     """The serving loop on Poisson traces (requests of 1-4 stages from the
     4-stage set over fresh seeded arrays, n log-uniform 2^10..2^24, budget
     64 GiB): continuous batching against plain per-request launches, at the
-    nominal 20 000 requests/s and at a saturating 80 000 requests/s."""
+    nominal 20 000 requests/s and at a saturating 80 000 requests/s. In the
+    batched modes a tick that holds one request runs that request's plain
+    launches; "batched_all" batches such ticks too."""
     import numpy as np
     import ka_inputs as ki
     s, sysh = ka.ka_system_create(0, budget_bytes=64 << 30)
@@ -730,8 +732,9 @@ def serve_large(ka, torch):
             reqs = ka.serve_requests(tr.arrival_s, tr.n, tr.seeds, stages)
             row = {"rate_per_s": rate, "duration_s": dur, "requests": len(tr.n),
                    "offered_elements/s": float(np.sum(tr.n)) / dur}
-            for mode, name in ((0, "batched"), (1, "plain"), (2, "batched_no_graph")):
-                s, res, stats = ka.serve(sysh, reqs, mode=mode)
+            for mode, flags, name in ((0, 0, "batched"), (1, 0, "plain"), (2, 0, "batched_no_graph"),
+                                      (0, ka.KA_SERVE_BATCH_LONE, "batched_all")):
+                s, res, stats = ka.serve(sysh, reqs, mode=mode, flags=flags)
                 ka.check(s)
                 lat = np.array([res[r].done_s - tr.arrival_s[r] for r in range(len(tr.n))])
                 row[name] = {"elements/s": stats.elements / stats.wall_s, "wall_s": round(stats.wall_s, 4),
@@ -740,6 +743,7 @@ def serve_large(ka, torch):
                              "p999_ms": round(1e3 * float(np.percentile(lat, 99.9)), 3),
                              "launches": int(stats.launches), "iterations": int(stats.iterations),
                              "peak_GB": round(stats.peak_bytes / 1e9, 3), "graph_launches": int(stats.graph_launches),
+                             "lone_ticks": int(stats.lone_ticks),
                              "ok": all(res[r].status == 0 for r in range(len(tr.n)))}
             out.append(row)
     finally:

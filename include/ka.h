@@ -479,7 +479,13 @@ typedef struct ka_serve_options {
     uint64_t budget_bytes;       /* admission budget (0: the system's)               */
     double time_scale;           /* arrival_s multiplier (1.0 = real time)           */
     ka_tile tile;                /* batched kernel shape ({0,0}: autotuned/default)  */
+    uint32_t flags;              /* KA_SERVE_* below (0: none)                       */
 } ka_serve_options;
+/* Modes 0 and 2 issue a tick that holds a single request as that request's
+ * plain launch sequence (generate, one compaction per stage, count
+ * publication), without the batch tables and plan kernels; this flag batches
+ * such a tick like any other. */
+#define KA_SERVE_BATCH_LONE 1u
 
 typedef struct ka_serve_stats {
     double wall_s;
@@ -490,6 +496,7 @@ typedef struct ka_serve_stats {
     uint32_t max_inflight_seen;
     uint32_t rejected;           /* requests larger than the whole budget            */
     uint64_t graph_launches;     /* ticks issued as one CUDA graph launch (mode 0)   */
+    uint64_t lone_ticks;         /* ticks of one request issued as plain launches    */
 } ka_serve_stats;
 
 ka_status ka_serve_run(ka_system *sys, const ka_serve_request *reqs, uint32_t n_reqs,

@@ -98,14 +98,14 @@ class ka_serve_result(ctypes.Structure):
 
 class ka_serve_options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("max_inflight", ctypes.c_uint32), ("budget_bytes", ctypes.c_uint64),
-                ("time_scale", ctypes.c_double), ("tile", ka_tile)]
+                ("time_scale", ctypes.c_double), ("tile", ka_tile), ("flags", ctypes.c_uint32)]
 
 
 class ka_serve_stats(ctypes.Structure):
     _fields_ = [("wall_s", ctypes.c_double), ("elements", ctypes.c_uint64), ("launches", ctypes.c_uint64),
                 ("iterations", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
                 ("max_inflight_seen", ctypes.c_uint32), ("rejected", ctypes.c_uint32),
-                ("graph_launches", ctypes.c_uint64)]
+                ("graph_launches", ctypes.c_uint64), ("lone_ticks", ctypes.c_uint64)]
 
 
 MONITOR_FN = ctypes.CFUNCTYPE(None, c_vp, ctypes.c_int32)
@@ -525,10 +525,13 @@ def serve_requests(arrival_s, n, seeds, stages):
     return arr
 
 
+KA_SERVE_BATCH_LONE = 1
+
+
 def serve(sys_h, reqs, mode: int = 0, budget_bytes: int = 0, max_inflight: int = 0, time_scale: float = 1.0,
-          tile=None):
+          tile=None, flags: int = 0):
     """Runs ka_serve_run; returns (status, results array, stats)."""
-    opt = ka_serve_options(mode, max_inflight, budget_bytes, time_scale, ka_tile(*(tile or (0, 0))))
+    opt = ka_serve_options(mode, max_inflight, budget_bytes, time_scale, ka_tile(*(tile or (0, 0))), flags)
     results = (ka_serve_result * max(len(reqs), 1))()
     stats = ka_serve_stats()
     st = lib.ka_serve_run(sys_h, reqs, len(reqs), ctypes.byref(opt), results, ctypes.byref(stats))

@@ -55,6 +55,7 @@ struct Tick {
     std::vector<uint32_t> reqs;  // request indices, tick position = vector index
     uint32_t depth = 0;          // stages of the deepest request
     bool busy = false;
+    bool lone = false;           // issued as one request's plain launches (errors in ws_plain)
     // graph mode: the tick's whole sequence for each depth, captured once;
     // host table entries past the current tick are kept zero (empty items)
     cudaGraphExec_t graph[kDepth] = {nullptr, nullptr, nullptr, nullptr};
@@ -110,6 +111,7 @@ struct Run {
     ka_tile batch_tile{0, 0};
     uint32_t grid_max = 0;  // blocks of a full persistent launch
     bool graphs = false;    // ticks replay captured graphs
+    bool batch_lone = false;  // a tick of one request is batched too (else plain launches)
 
     // plain mode
     struct Slot {
@@ -214,6 +216,43 @@ ka_status issue_tick(Run &R, bool *issued) {
     }
     if (T.reqs.empty()) return KA_OK;
     const uint32_t k = uint32_t(T.reqs.size());
+    T.lone = k == 1 && !R.batch_lone;
+    if (T.lone) {
+        // one request: its plain launch sequence into the tick's count table
+        const ka_serve_request &q = R.reqs[T.reqs[0]];
+        uint32_t *b = static_cast<uint32_t *>(R.buf[T.reqs[0]]);
+        cudaStream_t st = R.stream;
+        ka_status s = launch_generate(b, q.n, q.seed, nullptr, st);
+        R.st.launches += 1;
+        for (uint32_t d = 0; d < q.n_stages && s == KA_OK; ++d) {
+            CompactLaunch L;
+            s = make_pred(q.stages[d].pred, q.stages[d].param, &L.pred);
+            if (s != KA_OK) break;
+            L.in = b;
+            L.out = b;
+            L.n_ptr = d ? T.cnt(T.dev, int(d) - 1) : nullptr;
+            L.count = T.cnt(T.dev, int(d));
+            L.n = q.n;
+            L.mul = q.stages[d].xform == KA_XFORM_HASH ? kHashMul : 1u;
+            L.ws = R.ws_plain;
+            L.ws_bytes = R.ws_plain_bytes;
+            L.tile = resolve_tile(KA_KERNEL_COMPACT, q.n, nullptr);
+            s = launch_compact(L, st);
+            R.st.launches += 1;
+        }
+        if (s == KA_OK)
+            s = launch_publish(T.cnt(T.dev, 0), kTickItems * T.depth, 0, &static_cast<WsHeader *>(R.ws_plain)->error,
+                               T.cnt(T.host_dev, 0), T.err(T.host_dev), st);
+        R.st.launches += 1;
+        if (s == KA_OK) s = cuda_status(cudaEventRecord(T.ev, st));
+        if (s != KA_OK) return s;
+        T.busy = true;
+        R.tick_used += 1;
+        R.st.iterations += 1;
+        R.st.lone_ticks += 1;
+        *issued = true;
+        return KA_OK;
+    }
     uint32_t per_stage[kDepth] = {0, 0, 0, 0};
     uint64_t tiles[kDepth] = {0, 0, 0, 0};  // tiles of each stage launch: no more blocks than tiles
     const uint32_t te = R.batch_tile.block * R.batch_tile.ipt;
@@ -345,7 +384,8 @@ ka_status poll_ticks(Run &R, bool *progressed) {
             finish(R, r, T.cnt(T.host, int(last))[i], err ? -int32_t(err) : KA_OK);
         }
         if (err) {  // clear the error so later ticks are judged on their own
-            ka_status s = ka_workspace_init(R.ws_cmp, R.ws_cmp_bytes, R.stream);
+            ka_status s = T.lone ? ka_workspace_init(R.ws_plain, R.ws_plain_bytes, R.stream)
+                                 : ka_workspace_init(R.ws_cmp, R.ws_cmp_bytes, R.stream);
             if (s != KA_OK) return s;
         }
         T.busy = false;
@@ -437,6 +477,10 @@ ka_status setup(Run &R, uint32_t max_n) {
         if (s == KA_OK) s = cuda_status(cudaMalloc(&R.ws_cmp, R.ws_cmp_bytes));
         if (s == KA_OK) s = ka_workspace_init(R.ws_gen, R.ws_gen_bytes, R.stream);
         if (s == KA_OK) s = ka_workspace_init(R.ws_cmp, R.ws_cmp_bytes, R.stream);
+        // ticks of one request run the plain compaction on a workspace of their own
+        if (s == KA_OK) s = ka_workspace_size(max_n ? max_n : 1, nullptr, &R.ws_plain_bytes);
+        if (s == KA_OK) s = cuda_status(cudaMalloc(&R.ws_plain, R.ws_plain_bytes));
+        if (s == KA_OK) s = ka_workspace_init(R.ws_plain, R.ws_plain_bytes, R.stream);
         for (int i = 0; i < kTicks && s == KA_OK; ++i) {
             s = cuda_status(cudaMalloc(&R.ticks[i].dev, Tick::kBytes));
             if (s == KA_OK) s = cuda_status(cudaHostAlloc(&R.ticks[i].host, Tick::kBytes, cudaHostAllocMapped));
@@ -521,6 +565,7 @@ extern "C" ka_status ka_serve_run(ka_system *sys, const ka_serve_request *reqs, 
     R.max_inflight = opt->max_inflight ? opt->max_inflight : 4096;
     R.scale = opt->time_scale > 0 ? opt->time_scale : 1.0;
     R.tile = opt->tile;
+    R.batch_lone = (opt->flags & KA_SERVE_BATCH_LONE) != 0;
     R.buf.assign(n_reqs, nullptr);
     R.order.resize(n_reqs);
     uint32_t max_n = 0;

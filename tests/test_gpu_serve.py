@@ -50,8 +50,10 @@ def expected(tr, r):
     return y, len(y)
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
-def test_every_result_matches_the_oracle(ka, system, mode):
+@pytest.mark.parametrize("mode,flags", [(0, 0), (0, 1), (1, 0), (2, 0), (2, 1)])
+def test_every_result_matches_the_oracle(ka, system, mode, flags):
+    """flags 1 (KA_SERVE_BATCH_LONE): ticks of one request are batched too;
+    else they run as that request's plain launches."""
     tr, stages, reqs = trace(ka, 4000.0, 0.1, 8, 18)
     n = len(tr.n)
     assert n > 200
@@ -62,7 +64,7 @@ def test_every_result_matches_the_oracle(ka, system, mode):
         outs[r] = buf
         reqs[r].h_out = buf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
         reqs[r].h_out_cap = buf.size
-    s, res, stats = ka.serve(system, reqs, mode=mode)
+    s, res, stats = ka.serve(system, reqs, mode=mode, flags=flags)
     assert s == 0, ka.ka_strerror(s)
     assert stats.elements == int(np.sum(tr.n)) and stats.rejected == 0
     for r in range(n):
@@ -75,14 +77,20 @@ def test_every_result_matches_the_oracle(ka, system, mode):
         assert stats.iterations < n  # requests shared batched launches
     else:
         assert stats.iterations == n
+    if mode == 1 or flags:
+        assert stats.lone_ticks == 0
     if mode == 0:
-        assert stats.graph_launches == stats.iterations  # every tick was one graph launch
+        # every tick was one graph launch, or one request's plain launches
+        assert stats.graph_launches + stats.lone_ticks == stats.iterations
+        assert stats.graph_launches > 0
     else:
         assert stats.graph_launches == 0
 
 
-def test_same_result_alone_and_in_the_mix(ka, system):
-    """A request served alone and inside a busy trace gives the same count and data."""
+@pytest.mark.parametrize("flags", [0, 1])
+def test_same_result_alone_and_in_the_mix(ka, system, flags):
+    """A request served alone (as a tick of its own: plain launches, or batched
+    with flags 1) and inside a busy trace gives the same count and data."""
     tr, stages, reqs = trace(ka, 20000.0, 0.05, 10, 20, seed_off=1)
     s, mix, _ = ka.serve(system, reqs, mode=0)
     assert s == 0
@@ -91,7 +99,8 @@ def test_same_result_alone_and_in_the_mix(ka, system):
         buf_one = np.zeros(int(tr.n[r]), dtype=np.uint32)
         one[0].h_out = buf_one.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
         one[0].h_out_cap = buf_one.size
-        s, alone, _ = ka.serve(system, one, mode=0)
+        s, alone, st1 = ka.serve(system, one, mode=0, flags=flags)
+        assert st1.lone_ticks == (0 if flags else 1)
         assert s == 0 and alone[0].status == 0 and mix[r].status == 0
         assert alone[0].count == mix[r].count
         y, k = expected(tr, r)
