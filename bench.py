@@ -714,7 +714,9 @@ def serve_large(ka, torch):
     64 GiB): continuous batching against plain per-request launches, at the
     nominal 20 000 requests/s and at a saturating 80 000 requests/s. In the
     batched modes a tick that holds one request runs that request's plain
-    launches; "batched_all" batches such ticks too."""
+    launches; "batched_all" batches such ticks too. A saturation sweep then
+    raises the rate for the batched loop alone (plain launches already fall
+    behind at 80 000 requests/s) until its queue grows without bound."""
     import numpy as np
     import ka_inputs as ki
     s, sysh = ka.ka_system_create(0, budget_bytes=64 << 30)
@@ -746,6 +748,23 @@ def serve_large(ka, torch):
                              "lone_ticks": int(stats.lone_ticks),
                              "ok": all(res[r].status == 0 for r in range(len(tr.n)))}
             out.append(row)
+        sweep = []
+        for rate in (20000.0, 40000.0, 80000.0, 160000.0, 320000.0):
+            dur = 0.25
+            tr = ki.config_serve(rate, dur)
+            stages = [[spec(ki.PIPELINE4[int(k)]) for k in tr.stage_kind[r][:tr.n_stages[r]]]
+                      for r in range(len(tr.n))]
+            reqs = ka.serve_requests(tr.arrival_s, tr.n, tr.seeds, stages)
+            s, res, stats = ka.serve(sysh, reqs, mode=0)
+            ka.check(s)
+            lat = np.array([res[r].done_s - tr.arrival_s[r] for r in range(len(tr.n))])
+            sweep.append({"rate_per_s": rate, "requests": len(tr.n),
+                          "offered_elements/s": float(np.sum(tr.n)) / dur,
+                          "elements/s": stats.elements / stats.wall_s, "wall_s": round(stats.wall_s, 4),
+                          "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
+                          "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
+                          "ok": all(res[r].status == 0 for r in range(len(tr.n)))})
+        out.append({"saturation_sweep_batched": sweep})
     finally:
         ka.ka_system_destroy(sysh, 1)
     return out
