@@ -113,3 +113,31 @@ def test_product_never_imports_the_oracle():
             if f.endswith((".py", ".cu", ".cpp", ".h", ".cuh")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "ka_oracle" not in text, f
+
+
+def test_host_stream_scratch_size_and_refusals(ka):
+    """ka_compact_host's sizing and the argument checks it makes before any
+    device work: three rotating buffer sets (input and one output per
+    predicate) of whole 256-byte blocks, then the compaction workspace."""
+    r256 = lambda b: (b + 255) // 256 * 256  # noqa: E731
+    for chunk, p in ((1 << 24, 3), (1000, 1), (4, 4)):
+        s, b = ka.ka_compact_host_scratch_size(chunk, p)
+        ws = ka.ka_workspace_size(chunk)[1]
+        assert s == 0 and b == 3 * (1 + p) * r256(4 * chunk) + 3 * 256 + r256(ws)
+    assert ka.ka_compact_host_scratch_size(0, 2) == ka.ka_compact_host_scratch_size(1 << 24, 2)
+    assert ka.ka_compact_host_scratch_size(1 << 24, 0)[0] == ka.KA_E_ARG
+    assert ka.ka_compact_host_scratch_size(1 << 24, 5)[0] == ka.KA_E_ARG
+    assert ka.ka_compact_host_scratch_size(1 << 32, 1)[0] == ka.KA_E_ARG
+    x = np.arange(16, dtype=np.uint32)
+    out = [np.zeros(16, dtype=np.uint32)]
+    lt = ka.PRED["lt"]
+    _, b = ka.ka_compact_host_scratch_size(1024, 1)
+    fake = 1 << 40  # never dereferenced: every call below is refused first
+    assert ka.ka_compact_host(x, 16, [lt], [5], [0], out, 1024, fake, b - 1)[0] == ka.KA_E_WORKSPACE
+    assert ka.ka_compact_host(x, 16, [lt], [5], [0], out, 1024, fake + 8, b)[0] == ka.KA_E_ARG
+    assert ka.ka_compact_host(x, 16, [lt], [5], [9], out, 1024, fake, b)[0] == ka.KA_E_ARG
+    assert ka.ka_compact_host(None, 16, [lt], [5], [0], out, 1024, fake, b)[0] == ka.KA_E_ARG
+    assert ka.ka_compact_host(x, 16, [lt], [5], [0], [None], 1024, fake, b)[0] == ka.KA_E_ARG
+    assert ka.ka_compact_host(x, 16, [], [], [], [], 1024, fake, b)[0] == ka.KA_E_ARG
+    # n = 0 needs no device work: every count is 0
+    assert ka.ka_compact_host(x, 0, [lt, lt], [5, 6], [0, 0], out * 2, 1024, fake, 1 << 40) == (0, [0, 0])
