@@ -781,10 +781,21 @@ def cpu_baseline_large(kept_gpu, N):
         _, k = oracle.compact(x, "lt", ki.threshold_for(s_))
         ks.append(k)
     dt = time.perf_counter() - t0
+    # for context: a multi-threaded count / offsets / copy on every host core
+    # (oracle/cpu_mt.c; not the oracle)
+    from oracle import cpu_mt
+    threads = os.cpu_count() or 1
+    cpu_mt.compact_lt(x[:1 << 20], ki.threshold_for(0.5), threads)  # warm-up (threads, pages)
+    t1 = time.perf_counter()
+    ks_mt = [cpu_mt.compact_lt(x, ki.threshold_for(s_), threads)[1] for s_ in SELECTIVITIES]
+    dt_mt = time.perf_counter() - t1
     return {"value": 3.0 * N / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
             "host_cores_available": os.cpu_count(),
             "sample": "full workload: N=2^%d at s=1%%/50%%/99%%, one pass each (%.1f s)" % (N.bit_length() - 1, dt),
-            "counts_match_gpu": ks == list(kept_gpu)}
+            "counts_match_gpu": ks == list(kept_gpu),
+            "multithreaded_context": {"value": 3.0 * N / dt_mt, "unit": "elements/s", "threads": threads,
+                                      "kind": "count, offsets, copy with pthreads (not the oracle)",
+                                      "counts_match_gpu": ks_mt == list(kept_gpu)}}
 
 
 # ---------------------------------------------------------------------------
