@@ -191,9 +191,10 @@ ka_status ka_compact_static(const uint32_t *d_in, uint64_t n, const uint32_t *d_
                             const ka_tile *tile, void *stream);
 
 /* Three-phase compaction (Sec. 4.1: count, prefix sum, move, after Billeter
- * et al.): per-tile kept counts (tiles of 4096 entries), an exclusive scan
- * of the counts, then each kept entry moved to its tile's offset plus its rank
- * in the tile. Same result as ka_compact; reads the input twice. Workspace:
+ * et al.): per-segment kept counts (segments of 512 entries, one warp's
+ * share), an exclusive scan of the counts, then each kept entry moved to its
+ * segment's offset plus its rank in the segment. Same result as ka_compact;
+ * reads the input twice. Workspace:
  * ka_three_phase_workspace_size bytes, 256-byte aligned, initialised once
  * with ka_workspace_init. d_count must not alias d_n. */
 ka_status ka_three_phase_workspace_size(uint64_t capacity, uint64_t *bytes);
