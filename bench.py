@@ -323,6 +323,7 @@ def run_ours(args):
                              "plain_p50_ms": sv["plain"]["p50_ms"], "plain_p99_ms": sv["plain"]["p99_ms"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline_large(kept, N)
+        result["cpu_baseline"]["by_config"] = cpu_oracle_by_config()
     D.close()
     if rank == 0:
         print(json.dumps(result), flush=True)
@@ -796,6 +797,54 @@ def cpu_baseline_large(kept_gpu, N):
             "multithreaded_context": {"value": 3.0 * N / dt_mt, "unit": "elements/s", "threads": threads,
                                       "kind": "count, offsets, copy with pthreads (not the oracle)",
                                       "counts_match_gpu": ks_mt == list(kept_gpu)}}
+
+
+def cpu_oracle_by_config():
+    """The oracle (one host core) on each configuration's own inputs, bounded:
+    cfg1 in full, cfg3 in full, the first 512 instances of the 4096-instance
+    batch, and the first 200 requests of the serving trace (service time per
+    request: generate its array, run its stages)."""
+    import numpy as np
+    import oracle
+    import ka_inputs as ki
+    out = {"cores": 1, "kind": "oracle"}
+    w = ki.config_single()
+    x = oracle.generate(w.seed, w.n)
+    t0 = time.perf_counter()
+    reps = 20
+    for _ in range(reps):
+        _, k = oracle.compact(x, "and_mask_eq0", 3)
+    dt = (time.perf_counter() - t0) / reps
+    out["single_2^20"] = {"us": round(dt * 1e6, 1), "elements/s": w.n / dt, "kept": k}
+    w = ki.config_pipeline4()
+    x = oracle.generate(w.seed, w.n)
+    t0 = time.perf_counter()
+    ys = oracle.pipeline(x, w.stages)
+    dt = time.perf_counter() - t0
+    out["pipeline4_2^26"] = {"ms": round(dt * 1e3, 1), "elements/s": w.n / dt, "kept": int(ys[-1].size)}
+    b = ki.config_batch()
+    m = 512
+    xs = [oracle.generate(int(b.seeds[i]), int(b.n[i])) for i in range(m)]
+    t0 = time.perf_counter()
+    for i in range(m):
+        oracle.compact(xs[i], "lt", int(b.t[i]))
+    dt = time.perf_counter() - t0
+    el = int(np.sum(b.n[:m]))
+    out["batch_first_512_of_4096"] = {"ms": round(dt * 1e3, 1), "elements": el, "elements/s": el / dt}
+    tr = ki.config_serve(20000.0, 1.0)
+    m = 200
+    times = []
+    for r in range(m):
+        t1 = time.perf_counter()
+        xr = oracle.generate(int(tr.seeds[r]), int(tr.n[r]))
+        oracle.pipeline(xr, [ki.PIPELINE4[int(k)] for k in tr.stage_kind[r][:tr.n_stages[r]]])
+        times.append(time.perf_counter() - t1)
+    el = int(np.sum(tr.n[:m]))
+    out["serve_first_200_requests"] = {"mean_ms": round(1e3 * float(np.mean(times)), 3),
+                                       "p50_ms": round(1e3 * float(np.percentile(times, 50)), 3),
+                                       "p99_ms": round(1e3 * float(np.percentile(times, 99)), 3),
+                                       "elements/s": el / float(np.sum(times))}
+    return out
 
 
 # ---------------------------------------------------------------------------
