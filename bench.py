@@ -58,9 +58,12 @@ def parse_args():
     p.add_argument("--tile", default="", help="block,ipt: fix the tile shape instead of autotuning it")
     p.add_argument("--clock-interval-ms", type=int, default=100,
                    help="nvidia-smi sampling interval during the timed region (0: do not sample)")
-    p.add_argument("--only", choices=["", "scan", "batch"], default="",
-                   help="time one kernel alone (for profiling): the exclusive scan of --n flags, or the "
-                        "4096-instance batch; W warm-up and K timed launches")
+    p.add_argument("--only", choices=["", "scan", "batch", "serve"], default="",
+                   help="time one part alone: the exclusive scan of --n flags, or the 4096-instance batch "
+                        "(W warm-up and K timed launches, for profiling); or the serving comparison at "
+                        "20 000 requests/s for --serve-duration seconds")
+    p.add_argument("--serve-duration", type=float, default=1.0,
+                   help="seconds of the 20 000 requests/s serving trace (the configuration's full run is 60)")
     return p.parse_args()
 
 
@@ -709,7 +712,7 @@ def batch_large(ka, torch, peak):
             "counts_match": bool(np.array_equal(kept, kept2))}
 
 
-def serve_large(ka, torch):
+def serve_large(ka, torch, rates=((20000.0, 1.0), (80000.0, 0.5)), sweep=True, all_modes=True):
     """The serving loop on Poisson traces (requests of 1-4 stages from the
     4-stage set over fresh seeded arrays, n log-uniform 2^10..2^24, budget
     64 GiB): continuous batching against plain per-request launches, at the
@@ -728,15 +731,16 @@ def serve_large(ka, torch):
                 else (ka.PRED[stg.pred], stg.param, ka.KA_XFORM_NONE))
     out = []
     try:
-        for rate, dur in ((20000.0, 1.0), (80000.0, 0.5)):
+        for rate, dur in rates:
             tr = ki.config_serve(rate, dur)
             stages = [[spec(ki.PIPELINE4[int(k)]) for k in tr.stage_kind[r][:tr.n_stages[r]]]
                       for r in range(len(tr.n))]
             reqs = ka.serve_requests(tr.arrival_s, tr.n, tr.seeds, stages)
             row = {"rate_per_s": rate, "duration_s": dur, "requests": len(tr.n),
                    "offered_elements/s": float(np.sum(tr.n)) / dur}
-            for mode, flags, name in ((0, 0, "batched"), (1, 0, "plain"), (2, 0, "batched_no_graph"),
-                                      (0, ka.KA_SERVE_BATCH_LONE, "batched_all")):
+            modes = ((0, 0, "batched"), (1, 0, "plain"), (2, 0, "batched_no_graph"),
+                     (0, ka.KA_SERVE_BATCH_LONE, "batched_all"))
+            for mode, flags, name in (modes if all_modes else modes[:2]):
                 s, res, stats = ka.serve(sysh, reqs, mode=mode, flags=flags)
                 ka.check(s)
                 lat = np.array([res[r].done_s - tr.arrival_s[r] for r in range(len(tr.n))])
@@ -749,8 +753,8 @@ def serve_large(ka, torch):
                              "lone_ticks": int(stats.lone_ticks),
                              "ok": all(res[r].status == 0 for r in range(len(tr.n)))}
             out.append(row)
-        sweep = []
-        for rate in (20000.0, 40000.0, 80000.0, 160000.0, 320000.0):
+        points = []
+        for rate in ((20000.0, 40000.0, 80000.0, 160000.0, 320000.0) if sweep else ()):
             dur = 0.25
             tr = ki.config_serve(rate, dur)
             stages = [[spec(ki.PIPELINE4[int(k)]) for k in tr.stage_kind[r][:tr.n_stages[r]]]
@@ -759,13 +763,14 @@ def serve_large(ka, torch):
             s, res, stats = ka.serve(sysh, reqs, mode=0)
             ka.check(s)
             lat = np.array([res[r].done_s - tr.arrival_s[r] for r in range(len(tr.n))])
-            sweep.append({"rate_per_s": rate, "requests": len(tr.n),
+            points.append({"rate_per_s": rate, "requests": len(tr.n),
                           "offered_elements/s": float(np.sum(tr.n)) / dur,
                           "elements/s": stats.elements / stats.wall_s, "wall_s": round(stats.wall_s, 4),
                           "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
                           "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
                           "ok": all(res[r].status == 0 for r in range(len(tr.n)))})
-        out.append({"saturation_sweep_batched": sweep})
+        if sweep:
+            out.append({"saturation_sweep_batched": points})
     finally:
         ka.ka_system_destroy(sysh, 1)
     return out
@@ -953,8 +958,20 @@ def run_only(args):
                       "peak_kind": peak_kind}), flush=True)
 
 
+def run_serve_only(args):
+    """The serving comparison alone (batched against plain launches) at
+    20 000 requests/s for --serve-duration seconds; one JSON line."""
+    import torch
+    import paper_1709_07781_gb300 as ka
+    row = serve_large(ka, torch, rates=((20000.0, args.serve_duration),), sweep=False, all_modes=False)[0]
+    print(json.dumps({"only": "serve", **row}))
+
+
 def main():
     args = parse_args()
+    if args.only == "serve":
+        run_serve_only(args)
+        return
     if args.only:
         run_only(args)
         return
