@@ -383,7 +383,7 @@ ka_status poll_ticks(Run &R, bool *progressed) {
             const uint32_t last = R.reqs[r].n_stages - 1;
             finish(R, r, T.cnt(T.host, int(last))[i], err ? -int32_t(err) : KA_OK);
         }
-        if (err) {  // clear the error so later ticks are judged on their own
+        if (err) {  // clear the error so later ticks report only their own
             ka_status s = T.lone ? ka_workspace_init(R.ws_plain, R.ws_plain_bytes, R.stream)
                                  : ka_workspace_init(R.ws_cmp, R.ws_cmp_bytes, R.stream);
             if (s != KA_OK) return s;
