@@ -203,6 +203,23 @@ __global__ void __launch_bounds__(kGenBlock) k_generate_batch(const ka_gen_item 
 
 }  // namespace ka
 
+namespace ka {
+namespace {
+// Each flattened tile's item, into the spare word of the tile's status entry
+// (the TMA batch kernel's producer reads it ahead of time); one warp per item.
+__global__ void k_batch_tile_items(uint32_t n_items, BatchLayout L) {
+    const uint32_t total = L.tile_off[n_items];
+    if (total > L.status_cap) return;  // the plan kernel has recorded the error
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t stride = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n_items; i += stride) {
+        const uint32_t t1 = L.tile_off[i + 1];
+        for (uint32_t t = L.tile_off[i] + lane; t < t1; t += 32) *tile_item_at(L.status, t) = i;
+    }
+}
+}  // namespace
+}  // namespace ka
+
 using namespace ka;
 
 extern "C" {
@@ -240,7 +257,15 @@ ka_status ka_compact_batch(const ka_batch_item *d_items, uint32_t n_items, uint3
     k_batch_plan<<<1, kPlanBlock, 0, st>>>(d_items, n_items, t.block * t.ipt, a.L, a.ws, tma);
     ka_status s = cuda_status(cudaGetLastError());
     if (s != KA_OK) return s;
-    if (tma) return launch_batch_tma(a, t, grid, st);
+    if (tma) {
+        const uint64_t warps_needed = n_items, per_block = kPlanBlock / 32;
+        const uint64_t lim = uint64_t(device_info().sm_count) * 8;
+        const unsigned g = unsigned(std::min<uint64_t>((warps_needed + per_block - 1) / per_block, lim));
+        k_batch_tile_items<<<g, kPlanBlock, 0, st>>>(n_items, a.L);
+        s = cuda_status(cudaGetLastError());
+        if (s != KA_OK) return s;
+        return launch_batch_tma(a, t, grid, st);
+    }
     switch (shape_key(t.block, t.ipt)) {
 #define KA_CASE(B, I) \
     case shape_key(B, I): return launch_batch_shape<B, I>(a, grid, st);

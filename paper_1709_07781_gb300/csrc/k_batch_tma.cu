@@ -85,29 +85,58 @@ __global__ void __launch_bounds__((CWW + 2) * 32, MINB) k_batch_tma(const BatchA
 
     if (warp == CWW + 1) {
         // ------------------------------------------------------------------ producer warp
-        uint32_t hint = 0, issued = 0;
+        // The item of each flattened tile was written beside the tile's status
+        // word (k_batch_tile_items). Tile j + 2's item index and tile j + 1's
+        // item and plan records are loaded while tile j is issued, so no
+        // dependent load sits between two copies. A tile's records are spread
+        // over the warp, one word per lane: lanes 0-11 the item (48 bytes),
+        // 12-19 the plan (32 bytes), 20 the item's first tile.
+        uint32_t issued = 0;
         bool stop = false;
+        auto item_of = [&](uint32_t jj) -> uint32_t {  // every lane: the item of tile jj, or 0 past the end
+            return jj < my_tiles ? *tile_item_at(L.status, b + jj * G) : 0u;
+        };
+        auto record = [&](uint32_t i) -> uint32_t {  // this lane's word of item i's records
+            i = i < a.n_items ? i : 0u;                   // (a stale map cannot index past the items)
+            if (lane < 12) return reinterpret_cast<const uint32_t *>(a.items + i)[lane];
+            if (lane < 20) return reinterpret_cast<const uint32_t *>(L.plans + i)[lane - 12];
+            return lane == 20 ? L.tile_off[i] : 0u;
+        };
+        uint32_t idx1 = item_of(1), rec = record(item_of(0));
         for (uint32_t jj = 0; jj < my_tiles && !stop; ++jj) {
             const uint32_t tile = b + jj * G;
-            const uint32_t i = find_item(L.tile_off, a.n_items, hint, tile);
-            hint = i;
+            const uint32_t idx2 = item_of(jj + 2);
+            const uint32_t rec_next = jj + 1 < my_tiles ? record(idx1) : 0u;
+            // tile jj's records from the lanes that hold them
+            auto w = [&](int l) { return __shfl_sync(kFull, rec, l); };
+            const uint64_t in_u = uint64_t(w(0)) | (uint64_t(w(1)) << 32);
+            const uint64_t out_u = uint64_t(w(2)) | (uint64_t(w(3)) << 32);
+            const uint64_t cnt_u = uint64_t(w(6)) | (uint64_t(w(7)) << 32);
+            ItemPlan pl;
+            pl.pred.kind = int32_t(w(12));
+            pl.pred.a = w(13);
+            pl.pred.b = w(14);
+            pl.pred.c = w(15);
+            pl.pred.d = w(16);
+            pl.mul = w(17);
+            pl.n = w(18);
+            pl.tiles = w(19);
+            const uint32_t first = w(20);
             if (lane == 0) {
-                const ka_batch_item it = a.items[i];
-                const ItemPlan pl = L.plans[i];
-                const uint32_t first = L.tile_off[i];
-                const uint32_t lead = uint32_t(reinterpret_cast<uintptr_t>(it.in) & 15u) / 4u;
+                const uint32_t *in = reinterpret_cast<const uint32_t *>(in_u);
+                const uint32_t lead = uint32_t(in_u & 15u) / 4u;
                 const uint32_t local = tile - first;
                 const uint32_t nv = pl.n + lead, start = local * uint32_t(T);
                 TileInfo ti;
-                ti.out = it.out;
-                ti.count = it.count;
+                ti.out = reinterpret_cast<uint32_t *>(out_u);
+                ti.count = reinterpret_cast<uint32_t *>(cnt_u);
                 ti.pred = pl.pred;
                 ti.mul = pl.mul;
                 ti.first = first;
                 ti.last = first + pl.tiles - 1;
                 ti.vlo = local == 0 ? lead : 0u;
                 ti.vhi = min(nv - start, uint32_t(T));
-                const uint32_t *src = it.in - lead + start;
+                const uint32_t *src = in - lead + start;
                 const uint32_t bytes = (ti.vhi * 4u + 15u) & ~15u;
                 const int s = int(jj % S);
                 if (jj >= uint32_t(S) && !mbar_wait(&empty_bar[s], ((jj / S) - 1u) & 1u)) {
@@ -122,6 +151,8 @@ __global__ void __launch_bounds__((CWW + 2) * 32, MINB) k_batch_tma(const BatchA
                 }
             }
             stop = __shfl_sync(kFull, stop ? 1u : 0u, 0) != 0u;
+            rec = rec_next;
+            idx1 = idx2;
         }
         // Every copy has been consumed unless a wait gave up; wait (bounded)
         // for the last one on each stage so none lands after the block exits.

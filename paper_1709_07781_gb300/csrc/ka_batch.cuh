@@ -71,6 +71,15 @@ __device__ __forceinline__ uint32_t find_item(const uint32_t *tile_off, uint32_t
     return lo;
 }
 
+#ifdef __CUDACC__
+// The item of flattened tile t, kept in the spare second word of the tile's
+// status entry (the first word is the tile's status); written by
+// k_batch_tile_items before the TMA batch kernel runs.
+__device__ __forceinline__ uint32_t *tile_item_at(uint64_t *status, uint32_t t) {
+    return reinterpret_cast<uint32_t *>(status + uint64_t(t) * 4u + 1u);
+}
+#endif
+
 struct BatchArgs {
     const ka_batch_item *items;
     uint32_t n_items;
