@@ -78,7 +78,7 @@ def build(verbose: bool = False, force: bool = False, jobs: int | None = None) -
     if todo or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         tmp = LIB + ".tmp%d" % os.getpid()
         cmd = [os.path.join(cuda, "bin", "nvcc")] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + \
-            ["-lpthread"]
+            ["-lpthread", "-ldl"]  # libdl: NVTX looks up a profiler's injection library at run time
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -34,6 +34,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ka_internal.h"
 
 namespace ka {
@@ -455,6 +457,23 @@ static void fail_request(Msg *m, ka_status st) {
 }
 
 // Runs one stage for message m; on success fills outs/n_outs.
+// Name of a stage's NVTX range: each stage's launches show as one range on
+// the issuing thread in a profiler's timeline.
+static const char *stage_name(int32_t kind) {
+    switch (kind) {
+    case KA_STAGE_GENERATE: return "ka stage: generate";
+    case KA_STAGE_MAP_HASH: return "ka stage: map hash";
+    case KA_STAGE_PREDICATE: return "ka stage: predicate";
+    case KA_STAGE_EXSCAN: return "ka stage: exclusive scan";
+    case KA_STAGE_SCATTER: return "ka stage: scatter";
+    case KA_STAGE_COMPACT: return "ka stage: compact";
+    case KA_STAGE_PREPARE: return "ka stage: prepare index";
+    case KA_STAGE_EMPTY: return "ka stage: empty";
+    case KA_STAGE_MANDELBROT: return "ka stage: mandelbrot";
+    default: return "ka stage";
+    }
+}
+
 static ka_status run_stage(System *s, const StageSpec &sp, Msg *m, Ref **outs, int *n_outs) {
     cudaStream_t st = s->stream;
     *n_outs = 0;
@@ -595,7 +614,9 @@ static Actor *process(System *s, Actor *a, Msg *m) {
     }
     Ref *outs[KA_MSG_MAX_REFS];
     int n_outs = 0;
+    nvtxRangePushA(stage_name(a->spec.kind));
     const ka_status e = run_stage(s, a->spec, m, outs, &n_outs);
+    nvtxRangePop();
     if (e != KA_OK) {
         for (int i = 0; i < n_outs; ++i) ref_drop(outs[i]);
         fail_request(m, e);

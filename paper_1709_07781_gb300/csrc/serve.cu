@@ -33,6 +33,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ka_internal.h"
 
 namespace ka {
@@ -200,9 +202,19 @@ ka_status publish_counts(Run &R, Tick &T, uint32_t depth) {
                           T.cnt(T.host_dev, 0), T.err(T.host_dev), R.stream);
 }
 
+ka_status issue_tick_launches(Run &R, bool *issued);
+
+// One tick's launches, as one NVTX range on the serving thread.
 ka_status issue_tick(Run &R, bool *issued) {
     *issued = false;
     if (R.tick_used == kTicks || R.waiting.empty()) return KA_OK;
+    nvtxRangePushA("ka serve: tick");
+    const ka_status s = issue_tick_launches(R, issued);
+    nvtxRangePop();
+    return s;
+}
+
+ka_status issue_tick_launches(Run &R, bool *issued) {
     Tick &T = R.ticks[(R.tick_head + R.tick_used) % kTicks];
     T.reqs.clear();
     T.depth = 0;
