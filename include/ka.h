@@ -333,7 +333,10 @@ typedef enum ka_access { KA_READ = 1, KA_WRITE = 2, KA_READ_WRITE = 3 } ka_acces
 
 ka_status ka_system_create(const ka_config *cfg, ka_system **out);
 /* Stops the dispatcher. Fails with KA_E_ARG while requests are in flight
- * unless force != 0 (then they complete with KA_E_CLOSED). */
+ * unless force != 0 (then queued requests fail with KA_E_CLOSED and launched
+ * ones finish). Afterwards every handle of the system (its requests,
+ * references and actors) is invalid: calls on it return KA_E_STALE. Borrowed
+ * memory stays the caller's; pool memory is returned. */
 ka_status ka_system_destroy(ka_system *sys, int32_t force);
 /* Bytes of pool memory held by live references. */
 ka_status ka_system_pool_bytes(ka_system *sys, uint64_t *in_use, uint64_t *budget);

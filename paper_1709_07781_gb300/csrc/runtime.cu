@@ -125,6 +125,22 @@ class HandleTable {
         free_.push_back(slot);
         return o;
     }
+    // Removes every handle whose object satisfies pred; returns the objects.
+    template <class Pred>
+    std::vector<T *> remove_if(Pred pred) {
+        std::lock_guard<std::mutex> l(mu_);
+        std::vector<T *> out;
+        for (uint32_t i = 0; i < slots_.size(); ++i) {
+            Slot &e = slots_[i];
+            if (e.obj && pred(e.obj)) {
+                out.push_back(e.obj);
+                e.obj = nullptr;
+                e.gen++;
+                free_.push_back(i);
+            }
+        }
+        return out;
+    }
     std::mutex &mutex() { return mu_; }
     T *get_locked(uint64_t h) {
         const uint64_t s = h & 0xFFFFFFFFu;
@@ -948,6 +964,20 @@ ka_status ka_system_destroy(ka_system *h, int32_t force) {
     s->comp_cv.notify_all();
     if (s->completer.joinable()) s->completer.join();
     cudaStreamSynchronize(s->stream);
+    // Every handle of this system becomes stale (KA_E_STALE from then on):
+    // requests never received (their results and actors released), the
+    // caller's references (pool memory returned), and the actors.
+    for (Request *r : g_requests.remove_if([s](Request *r) { return r->sys == s; })) {
+        for (Ref *x : r->result) ref_drop(x);
+        for (Actor *a : r->stages) actor_drop(a);
+        if (r->event) cudaEventDestroy(r->event);
+        delete r;
+    }
+    for (Ref *r : g_refs.remove_if([s](Ref *r) { return r->sys == s; })) {
+        if (r->bytes) cudaFreeAsync(r->block, s->stream);
+        delete r;
+    }
+    for (Actor *a : g_actors.remove_if([s](Actor *a) { return a->sys == s; })) actor_drop(a);
     cache_flush(s);
     if (s->ws) cudaFreeAsync(s->ws, s->stream);
     cudaStreamSynchronize(s->stream);
@@ -958,8 +988,6 @@ ka_status ka_system_destroy(ka_system *h, int32_t force) {
     if (s->pinned) cudaFreeHost(s->pinned);
     cudaStreamDestroy(s->readback);
     if (s->own_stream) cudaStreamDestroy(s->stream);
-    // Pool memory still held by references the caller never released stays
-    // valid until the pool is destroyed here.
     cudaMemPoolDestroy(s->pool);
     delete s;
     return KA_OK;

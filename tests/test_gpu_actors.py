@@ -441,3 +441,40 @@ def test_receiver_that_blocks_gets_result(ka, system):
             ka.ka_ref_release(m.refs[j])
     assert ka.ka_system_pool_bytes(system)[1] == 0
     ka.ka_actor_release(a)
+
+
+def test_destroy_with_requests_in_flight_makes_every_handle_stale(ka):
+    """Destroying a system with requests still in flight (force) finishes or
+    fails them; afterwards its request, reference and actor handles return
+    KA_E_STALE instead of touching freed state, and a new system works."""
+    s, sys_h = ka.ka_system_create(0)
+    assert s == 0
+    gen = spawn(ka, sys_h, ka.KA_STAGE_GENERATE)
+    comp = spawn(ka, sys_h, ka.KA_STAGE_COMPACT, ka.KA_PRED_LT, 1 << 31)
+    pipe = compose(ka, comp, gen)
+    reqs = []
+    for i in range(8):
+        s, q = ka.ka_request(pipe, ka.make_msg(seed=i, gen_n=1 << 22))
+        assert s == 0
+        reqs.append(q)
+    s, rx = ka.ka_ref_alloc(sys_h, 1 << 20)
+    assert s == 0
+    assert ka.ka_system_destroy(sys_h, 1) == 0
+    for q in reqs:
+        assert ka.ka_receive(q, 0)[0] == ka.KA_E_STALE
+    assert ka.ka_ref_release(rx) == ka.KA_E_STALE
+    assert ka.ka_ref_info(rx)[0] == ka.KA_E_STALE
+    assert ka.ka_request(pipe, ka.make_msg(seed=1, gen_n=16))[0] == ka.KA_E_STALE
+    for a in (pipe, gen, comp):
+        assert ka.ka_actor_release(a) == ka.KA_E_STALE
+    assert ka.ka_system_destroy(sys_h, 1) == ka.KA_E_STALE
+    # a fresh system is unaffected
+    s, sys2 = ka.ka_system_create(0)
+    assert s == 0
+    g2 = spawn(ka, sys2, ka.KA_STAGE_GENERATE)
+    s, q = ka.ka_request(g2, ka.make_msg(seed=3, gen_n=1000))
+    s, m = ka.ka_receive(q)
+    assert s == 0 and m.count == 1000
+    ka.ka_ref_release(m.refs[0])
+    ka.ka_actor_release(g2)
+    assert ka.ka_system_destroy(sys2, 0) == 0
