@@ -1302,7 +1302,10 @@ ka_status ka_receive(ka_request_h *h, int64_t timeout_ns, ka_msg *out) {
         System *s = r->sys;
         r->waiting.store(true, std::memory_order_release);
         const auto t0 = std::chrono::steady_clock::now();
-        const auto spin = std::chrono::microseconds(kReceiveSpinUs);
+        // (a time-out shorter than the spin window bounds the spin too)
+        const auto spin = timeout_ns >= 0 && timeout_ns < int64_t(kReceiveSpinUs) * 1000
+                              ? std::chrono::nanoseconds(timeout_ns)
+                              : std::chrono::nanoseconds(int64_t(kReceiveSpinUs) * 1000);
         while (!r->done.load(std::memory_order_acquire) && std::chrono::steady_clock::now() - t0 < spin) {
             if (!r->recorded.load(std::memory_order_acquire) || r->claimed.load(std::memory_order_acquire)) continue;
             const cudaError_t q = cudaEventQuery(r->event);
@@ -1315,8 +1318,9 @@ ka_status ka_receive(ka_request_h *h, int64_t timeout_ns, ka_msg *out) {
             std::unique_lock<std::mutex> l(r->mu);
             if (timeout_ns < 0) {
                 r->cv.wait(l, [&] { return r->done.load(); });
-            } else if (!r->cv.wait_for(l, std::chrono::nanoseconds(timeout_ns), [&] { return r->done.load(); })) {
-                return KA_E_TIMEOUT;
+            } else {
+                const auto left = std::chrono::nanoseconds(timeout_ns) - (std::chrono::steady_clock::now() - t0);
+                if (!r->cv.wait_for(l, left, [&] { return r->done.load(); })) return KA_E_TIMEOUT;
             }
         }
     }
