@@ -478,3 +478,25 @@ def test_destroy_with_requests_in_flight_makes_every_handle_stale(ka):
     ka.ka_ref_release(m.refs[0])
     ka.ka_actor_release(g2)
     assert ka.ka_system_destroy(sys2, 0) == 0
+
+
+def test_receive_time_out_bounds_the_wait(ka, system):
+    """A time-out of 0 polls (returns at once, not after the spin window);
+    a short time-out on a long request expires; then the result arrives."""
+    import time
+    a = spawn(ka, system, ka.KA_STAGE_MANDELBROT, 8192, 2000, 4096)  # about 25 ms of GPU work
+    s, q = ka.ka_request(a, ka.make_msg())
+    assert s == 0
+    t0 = time.perf_counter()
+    s, _ = ka.ka_receive(q, 0)
+    dt = time.perf_counter() - t0
+    assert s == ka.KA_E_TIMEOUT and dt < 1e-3, dt
+    t0 = time.perf_counter()
+    s, _ = ka.ka_receive(q, 300_000)  # 0.3 ms
+    dt = time.perf_counter() - t0
+    assert s == ka.KA_E_TIMEOUT and dt < 5e-3, dt
+    s, m = ka.ka_receive(q, -1)
+    assert s == 0 and m.count == 8192 * 4096
+    for j in range(m.n_refs):
+        ka.ka_ref_release(m.refs[j])
+    ka.ka_actor_release(a)
