@@ -141,6 +141,39 @@ def test_four_stage_pipeline_matches_oracle_and_direct(ka, system, fused_map):
         ka.ka_actor_release(a)
 
 
+@pytest.mark.parametrize("fused_map", [False, True])
+def test_four_stage_pipeline_full_size(ka, system, fused_map):
+    """The 4-stage workload at its full size (N = 2^26, seed 3), device
+    references as the overhead comparison runs it: the last stage's data and
+    count equal the oracle's."""
+    w = ki.config_pipeline4()
+    x = torch.empty(w.n, dtype=torch.int32, device="cuda")
+    assert ka.ka_generate(x, w.n, w.seed, stream()) == 0
+    torch.cuda.synchronize()
+    stages = []
+    if fused_map:
+        stages.append(spawn(ka, system, ka.KA_STAGE_COMPACT, ka.KA_PRED_TOPBITS_LT, 8, ka.KA_XFORM_HASH))
+    else:
+        stages.append(spawn(ka, system, ka.KA_STAGE_MAP_HASH))
+        stages.append(spawn(ka, system, ka.KA_STAGE_COMPACT, ka.KA_PRED_TOPBITS_LT, 8))
+    stages.append(spawn(ka, system, ka.KA_STAGE_COMPACT, ka.KA_PRED_POPC_ODD, 0))
+    stages.append(spawn(ka, system, ka.KA_STAGE_COMPACT, ka.KA_PRED_MOD_NE0, 3))
+    pipe = compose(ka, *reversed(stages))
+    s, rx = ka.ka_ref_wrap(system, x, w.n, w.n)
+    assert s == 0
+    s, req = ka.ka_request(pipe, ka.make_msg([rx]))
+    assert s == 0
+    s, msg = ka.ka_receive(req)
+    assert s == 0, ka.ka_strerror(s)
+    expect = oracle.pipeline(oracle.generate(w.seed, w.n), w.stages)[-1]
+    assert msg.count == expect.size and msg.n_refs == 1
+    assert np.array_equal(result_data(ka, msg.refs[0], msg.count), expect)
+    ka.ka_ref_release(msg.refs[0])
+    ka.ka_ref_release(rx)
+    for a in [pipe] + stages:
+        ka.ka_actor_release(a)
+
+
 def test_generate_stage_and_empty_stage(ka, system):
     gen = spawn(ka, system, ka.KA_STAGE_GENERATE)
     nop = spawn(ka, system, ka.KA_STAGE_EMPTY)

@@ -127,3 +127,37 @@ def test_invalid_stage_is_reported(ka, system):
     assert s == 0
     assert res[0].status == ka.KA_E_ARG
     assert res[1].status == 0 and res[1].count == oracle.compact(oracle.generate(2, 1000), "ne", 0)[1]
+
+
+@pytest.mark.parametrize("mode,flags", [(0, 0), (1, 0)])
+def test_full_size_trace_sampled(ka, mode, flags):
+    """The timed serving workload itself (20 000 requests/s for 1 s, sizes
+    2^10..2^24, 1-4 stages, a 64 GiB budget): every request succeeds, every
+    element is counted, and a deterministic sample (the four largest requests
+    and 24 spread over the trace) returns the oracle's data."""
+    s, sysh = ka.ka_system_create(0, budget_bytes=64 << 30)
+    assert s == 0, ka.ka_strerror(s)
+    try:
+        tr = ki.config_serve(20000.0, 1.0)
+        stages = [[stage_spec(ka, ki.PIPELINE4[int(k)]) for k in tr.stage_kind[r][:tr.n_stages[r]]]
+                  for r in range(len(tr.n))]
+        reqs = ka.serve_requests(tr.arrival_s, tr.n, tr.seeds, stages)
+        n = len(tr.n)
+        assert n > 15000 and int(np.max(tr.n)) > (1 << 23)
+        sample = sorted(set(np.argsort(tr.n)[-4:].tolist()) | set(np.linspace(0, n - 1, 24).astype(int).tolist()))
+        outs = {}
+        for r in sample:
+            buf = np.zeros(int(tr.n[r]) + 1, dtype=np.uint32)
+            outs[r] = buf
+            reqs[r].h_out = buf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+            reqs[r].h_out_cap = buf.size
+        s, res, stats = ka.serve(sysh, reqs, mode=mode, flags=flags)
+        assert s == 0, ka.ka_strerror(s)
+        assert stats.elements == int(np.sum(tr.n)) and stats.rejected == 0
+        assert all(res[r].status == 0 for r in range(n))
+        for r in sample:
+            y, k = expected(tr, r)
+            assert res[r].count == k, (r, res[r].count, k)
+            assert np.array_equal(outs[r][:k], y) and outs[r][k] == 0, r
+    finally:
+        assert ka.ka_system_destroy(sysh, 1) == 0
