@@ -196,7 +196,9 @@ ka_status ka_compact_static(const uint32_t *d_in, uint64_t n, const uint32_t *d_
  * segment's offset plus its rank in the segment. Same result as ka_compact;
  * reads the input twice. Workspace:
  * ka_three_phase_workspace_size bytes, 256-byte aligned, initialised once
- * with ka_workspace_init. d_count must not alias d_n. */
+ * with ka_workspace_init; ka_workspace_status on it reports a device-side
+ * failure (a look-back of the counts' scan that gave up). d_count must not
+ * alias d_n. */
 ka_status ka_three_phase_workspace_size(uint64_t capacity, uint64_t *bytes);
 ka_status ka_compact_three_phase(const uint32_t *d_in, uint64_t n, const uint32_t *d_n, int32_t pred,
                                  uint32_t param, uint32_t xform, uint32_t *d_out, uint32_t *d_count,

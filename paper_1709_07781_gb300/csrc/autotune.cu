@@ -103,12 +103,16 @@ bool load_table(const char *path) {
 
 ka_tile resolve_tile(int32_t kernel, uint64_t n, const ka_tile *requested) {
     if (requested && requested->block && requested->ipt) return *requested;
+    ka_tile t = default_tile(kernel, n);
     {
         std::lock_guard<std::mutex> lock(g_mu);
         auto it = g_table.find({kernel, bucket_of(n)});
-        if (it != g_table.end()) return it->second.first;
+        if (it != g_table.end()) t = it->second.first;
     }
-    return default_tile(kernel, n);
+    // The TMA kernels take at most 2^32 - 4 entries (their tiles start on a
+    // 16-byte boundary); above that, a shape the register kernels also have.
+    if (kernel != KA_KERNEL_BATCH && !tile_supported(t.block, t.ipt) && n > 0xFFFFFFFCull) t = ka_tile{512, 16};
+    return t;
 }
 
 // Times `launch` over `reps` runs after `warm` untimed runs; returns the median

@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kPlanBlock) k_gen_plan(const ka_gen_item *item
     for (uint32_t base = 0; base < n_items; base += kPlanBlock) {
         const uint32_t i = base + threadIdx.x;
         uint32_t tiles = 0;
-        if (i < n_items) tiles = (items[i].n + kGenTile - 1) / kGenTile;
+        if (i < n_items) tiles = uint32_t((uint64_t(items[i].n) + kGenTile - 1) / kGenTile);
         uint32_t block_total;
         const uint32_t excl = block_excl_scan(tiles, s_warp, &block_total);
         if (i < n_items) L.tile_off[i] = carry + excl;
@@ -193,9 +193,10 @@ __global__ void __launch_bounds__(kGenBlock) k_generate_batch(const ka_gen_item 
         __syncthreads();
         item = s_item;
         const ka_gen_item it = items[item];
-        const uint32_t base = (t - tile_off[item]) * kGenTile;
-        const uint32_t end = it.n - base < kGenTile ? it.n : base + kGenTile;
-        for (uint32_t e = base + threadIdx.x; e < end; e += kGenBlock)
+        // 64-bit positions: an item may hold up to 2^32 - 1 entries
+        const uint64_t base = uint64_t(t - tile_off[item]) * kGenTile;
+        const uint64_t end = it.n - base < kGenTile ? uint64_t(it.n) : base + kGenTile;
+        for (uint64_t e = base + threadIdx.x; e < end; e += kGenBlock)
             it.out[e] = uint32_t(splitmix64_b(it.seed, e) >> 32);
         __syncthreads();
     }

@@ -126,7 +126,8 @@ __global__ void __launch_bounds__((CWW + 2) * 32, MINB) k_batch_tma(const BatchA
                 const uint32_t *in = reinterpret_cast<const uint32_t *>(in_u);
                 const uint32_t lead = uint32_t(in_u & 15u) / 4u;
                 const uint32_t local = tile - first;
-                const uint32_t nv = pl.n + lead, start = local * uint32_t(T);
+                // 64-bit: an item of up to 2^32 - 1 entries plus its lead
+                const uint64_t nv = uint64_t(pl.n) + lead, start = uint64_t(local) * T;
                 TileInfo ti;
                 ti.out = reinterpret_cast<uint32_t *>(out_u);
                 ti.count = reinterpret_cast<uint32_t *>(cnt_u);
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__((CWW + 2) * 32, MINB) k_batch_tma(const BatchA
                 ti.first = first;
                 ti.last = first + pl.tiles - 1;
                 ti.vlo = local == 0 ? lead : 0u;
-                ti.vhi = min(nv - start, uint32_t(T));
+                ti.vhi = uint32_t(min(nv - start, uint64_t(T)));
                 const uint32_t *src = in - lead + start;
                 const uint32_t bytes = (ti.vhi * 4u + 15u) & ~15u;
                 const int s = int(jj % S);

@@ -6,7 +6,9 @@
 // All are HBM-bound streams: grid-stride loops over 16-byte vectors with two
 // vectors in flight per thread, grids of a few blocks per SM, scalar code for
 // the ragged head/tail and for inputs that are not 16-byte aligned. Live
-// lengths may come from a device word (the previous stage's count).
+// lengths may come from a device word (the previous stage's count). Scalar
+// entry indices are 64-bit: with n near 2^32, a 32-bit index plus the grid
+// stride would wrap below n and the loop would not end.
 #include "ka_internal.h"
 
 namespace ka {
@@ -55,9 +57,9 @@ __global__ void __launch_bounds__(kEwBlock) k_generate(uint32_t *out, uint32_t n
             v.w = uint32_t(splitmix64_dev(seed, e + 3) >> 32);
             st_v4(out + e, v);
         }
-        for (uint32_t e = n4 * 4 + tid; e < n; e += stride) out[e] = uint32_t(splitmix64_dev(seed, e) >> 32);
+        for (uint64_t e = uint64_t(n4) * 4 + tid; e < n; e += stride) out[e] = uint32_t(splitmix64_dev(seed, e) >> 32);
     } else {
-        for (uint32_t e = tid; e < n; e += stride) out[e] = uint32_t(splitmix64_dev(seed, e) >> 32);
+        for (uint64_t e = tid; e < n; e += stride) out[e] = uint32_t(splitmix64_dev(seed, e) >> 32);
     }
 }
 
@@ -91,9 +93,9 @@ __global__ void __launch_bounds__(kEwBlock) k_map(const uint32_t *in, uint64_t c
             const uint4 a = ld_stream_v4(in + uint64_t(i) * 4);
             st_v4(out + uint64_t(i) * 4, make_uint4(f(a.x), f(a.y), f(a.z), f(a.w)));
         }
-        for (uint32_t e = n4 * 4 + tid; e < n; e += stride) out[e] = f(in[e]);
+        for (uint64_t e = uint64_t(n4) * 4 + tid; e < n; e += stride) out[e] = f(in[e]);
     } else {
-        for (uint32_t e = tid; e < n; e += stride) out[e] = f(in[e]);
+        for (uint64_t e = tid; e < n; e += stride) out[e] = f(in[e]);
     }
 }
 

@@ -12,8 +12,10 @@
 // The move stages a segment's kept entries in the warp's own 2 KiB of shared
 // memory and stores them 16 bytes at a time, realigned to the output.
 //
-// Workspace: segment counts [segments], segment offsets [segments], the live
-// segment count, then a workspace for the scan of the counts.
+// Workspace: first the workspace of the scan of the counts (its header is the
+// workspace's header, so ka_workspace_status reports the scan's device-side
+// failures), then segment counts [segments], segment offsets [segments] and
+// the live segment count.
 #include "ka_internal.h"
 #include "ka_tma.cuh"
 
@@ -34,30 +36,37 @@ struct TpLayout {
 
 uint64_t r256(uint64_t b) { return (b + 255) / 256 * 256; }
 
-TpLayout tp_layout(void *ws, uint64_t tiles, uint64_t ws_bytes) {
+// Scan workspace for `tiles` segment counts (sized for the smallest tile).
+uint64_t tp_scan_bytes(uint64_t tiles) { return r256(workspace_bytes_for_tiles(tiles_for(tiles, 512) + 1)); }
+
+TpLayout tp_layout(void *ws, uint64_t tiles) {
     TpLayout L;
     char *p = static_cast<char *>(ws);
+    L.scan_ws = p;
+    L.scan_ws_bytes = tp_scan_bytes(tiles);
+    p += L.scan_ws_bytes;
     L.counts = reinterpret_cast<uint32_t *>(p);
     p += r256(tiles * 4);
     L.offsets = reinterpret_cast<uint32_t *>(p);
     p += r256(tiles * 4);
     L.n_tiles = reinterpret_cast<uint32_t *>(p);
-    p += 256;
-    L.scan_ws = p;
-    const uint64_t used = uint64_t(p - static_cast<char *>(ws));
-    L.scan_ws_bytes = ws_bytes > used ? ws_bytes - used : 0;
     return L;
 }
 
 uint64_t tp_bytes(uint64_t capacity) {
     const uint64_t tiles = tiles_for(capacity ? capacity : 1, kTpTile);
-    return 2 * r256(tiles * 4) + 256 + workspace_bytes_for_tiles(tiles_for(tiles, 512) + 1);
+    return tp_scan_bytes(tiles) + 2 * r256(tiles * 4) + 256;
 }
 
 __device__ __forceinline__ uint32_t tp_live(const uint32_t *n_ptr, uint32_t n) {
     if (!n_ptr) return n;
     const uint32_t d = *n_ptr;
     return d < n ? d : n;
+}
+
+// Segments of n entries (64-bit sum: n may be up to 2^32 - 1).
+__device__ __forceinline__ uint32_t tp_segments(uint32_t n) {
+    return uint32_t((uint64_t(n) + kTpSeg - 1) / kTpSeg);
 }
 
 // This lane's 16 entries of the segment at seg_in (valid entries: the first
@@ -102,7 +111,7 @@ __device__ __forceinline__ void tp_prefetch(const uint32_t *seg_in, int lane, ui
 template <class Body>
 __device__ __forceinline__ void tp_walk(const uint32_t *in, uint32_t n, bool vec, uint32_t seg0, uint32_t stride,
                                         int lane, Body body) {
-    const uint32_t segs = (n + kTpSeg - 1) / kTpSeg, full = n / kTpSeg;
+    const uint32_t segs = tp_segments(n), full = n / kTpSeg;
     uint4 cur[4], nxt[4];
     if (vec && seg0 < full) tp_prefetch(in + size_t(seg0) * kTpSeg, lane, nxt);
     for (uint32_t seg = seg0; seg < segs; seg += stride) {
@@ -120,7 +129,7 @@ constexpr int kTpBlocksPerSm = 4;  // each warp keeps two segments' loads in fli
 __global__ void __launch_bounds__(kTpBlock, kTpBlocksPerSm) k_tp_count(const uint32_t *in, uint32_t cap, const uint32_t *n_ptr,
                                                         PredDev pred, uint32_t mul, int vec, TpLayout L) {
     const uint32_t n = tp_live(n_ptr, cap);
-    const uint32_t segs = (n + kTpSeg - 1) / kTpSeg;
+    const uint32_t segs = tp_segments(n);
     if (blockIdx.x == 0 && threadIdx.x == 0) *L.n_tiles = segs;
     const int lane = threadIdx.x & 31;
     tp_walk(in, n, vec != 0, blockIdx.x * kTpWarps + (threadIdx.x >> 5), gridDim.x * kTpWarps, lane,
@@ -199,12 +208,12 @@ ka_status ka_compact_three_phase(const uint32_t *d_in, uint64_t n, const uint32_
     ka_status s = make_pred(pred, param, &p);
     if (s != KA_OK) return s;
     const uint64_t tiles = tiles_for(n ? n : 1, kTpTile);
-    const TpLayout L = tp_layout(d_ws, tiles, ws_bytes);
+    const TpLayout L = tp_layout(d_ws, tiles);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const uint32_t mul = xform == KA_XFORM_HASH ? kHashMul : 1u;
     const int vec = (reinterpret_cast<uintptr_t>(d_in) & 15u) == 0 ? 1 : 0;
-    // the scan's workspace starts zeroed on the first use of this workspace;
-    // its epoch tags make later launches safe without clearing
+    // the scan's workspace is the one ka_workspace_init prepared; its epoch
+    // tags make later launches safe without clearing
     k_tp_count<<<tp_grid(n, kTpBlocksPerSm), kTpBlock, 0, st>>>(d_in, uint32_t(n), d_n, p, mul, vec, L);
     s = cuda_status(cudaGetLastError());
     if (s != KA_OK) return s;

@@ -237,9 +237,9 @@ __device__ __forceinline__ void tma_pass(const TmaArgs &a) {
                     warp_copy_out(seg_base + size_t(s) * T, a.out + off, cnt, lane);
             } else if (ok && s_err[k] == 0u) {
                 // every input entry of the segment, plus the segment's offset, at its own index
-                const uint32_t base = (b + jp * G) * uint32_t(T) + uint32_t(w) * kSeg;
-                const uint32_t vlo = base < a.lead ? a.lead - base : 0u;
-                const uint32_t vhi = n > base ? min(n - base, uint32_t(kSeg)) : 0u;
+                const uint64_t base = uint64_t(b + jp * G) * T + uint32_t(w) * kSeg;
+                const uint32_t vlo = base < a.lead ? a.lead - uint32_t(base) : 0u;
+                const uint32_t vhi = n > base ? uint32_t(min(n - base, uint64_t(kSeg))) : 0u;
                 const uint32_t *sg = seg_base + size_t(s) * T;
                 uint32_t *dst = a.out - a.lead + base;  // entry i of the output is a.out[i]
 #pragma unroll
@@ -267,10 +267,12 @@ __device__ __forceinline__ void tma_pass(const TmaArgs &a) {
             const uint32_t tile = b + j * G, k = j & 3u;
             const int s = int(j % S);
             uint32_t *seg = seg_base + size_t(s) * T;
-            // entries [vlo, vhi) of this segment are input entries
-            const uint32_t base = tile * uint32_t(T) + uint32_t(w) * kSeg;
-            const uint32_t vlo = base < a.lead ? a.lead - base : 0u;
-            const uint32_t vhi = n > base ? min(n - base, uint32_t(kSeg)) : 0u;
+            // entries [vlo, vhi) of this segment are input entries (64-bit
+            // position: the last tile's later segments can lie past 2^32 when
+            // T does not divide 2^32)
+            const uint64_t base = uint64_t(tile) * T + uint32_t(w) * kSeg;
+            const uint32_t vlo = base < a.lead ? a.lead - uint32_t(base) : 0u;
+            const uint32_t vhi = n > base ? uint32_t(min(n - base, uint64_t(kSeg))) : 0u;
             if (tile < full_tiles) {
                 if (!mbar_wait(&full_bar[s], (j / S) & 1u) && lane == 0) record_error(a.ws, kDevErrTimeout, tile);
             } else {

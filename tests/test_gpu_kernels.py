@@ -408,6 +408,7 @@ def three_phase(ka, d_x, n, pred, param, xform=0, d_n=None, ws=None, cap=None):
                                   ws[1], ws[2], stream())
     assert s == 0, ka.ka_strerror(s)
     torch.cuda.synchronize()
+    assert ka.ka_workspace_status(ws[1], stream()) == (0, 0)
     return out, word(count), ws
 
 
