@@ -442,7 +442,10 @@ def actor_overhead(ka, torch):
     the same kernels launched directly, one pipeline after another, each
     waiting for its result count on the host: the 3-actor pipeline (N = 2^20,
     keep (x & 3) == 0), its fused single-actor form, and the 4-stage pipeline
-    (N = 2^26: hash, keep top bits < 8, keep popc odd, keep % 3 != 0)."""
+    (N = 2^26: hash, keep top bits < 8, keep popc odd, keep % 3 != 0).
+    Two direct loops: one waits with cudaStreamSynchronize (plain CUDA code,
+    `overhead_pct`), the other with the wait the receiver uses, a completion
+    tag polled in host memory (`layer_overhead_pct`: the actor layer alone)."""
     import ka_inputs as ki
     P = ka.PRED
     cases = [
@@ -483,11 +486,15 @@ def actor_overhead(ka, torch):
             ka.check(s)
             s, t_direct, k_direct = ka.ka_bench_direct_chain(specs, x, n, iters)
             ka.check(s)
-            us_a, us_d = t_actor / iters * 1e6, t_direct / iters * 1e6
+            s, t_tag, k_tag = ka.ka_bench_direct_chain(specs, x, n, iters, flags=ka.KA_BENCH_WAIT_TAG)
+            ka.check(s)
+            us_a, us_d, us_t = t_actor / iters * 1e6, t_direct / iters * 1e6, t_tag / iters * 1e6
             out.append({"pipeline": name, "n": n, "iters": iters, "actor_us": round(us_a, 2),
                         "direct_us": round(us_d, 2), "overhead_pct": round(100.0 * (us_a / us_d - 1.0), 2),
+                        "direct_same_wait_us": round(us_t, 2),
+                        "layer_overhead_pct": round(100.0 * (us_a / us_t - 1.0), 2),
                         "actor_elements/s": n / (us_a * 1e-6), "count": int(k_actor),
-                        "counts_match": int(k_actor) == int(k_direct)})
+                        "counts_match": int(k_actor) == int(k_direct) == int(k_tag)})
             ka.ka_ref_release(ref)
             for a in ([pipe] if len(actors) > 1 else []) + actors:
                 ka.ka_actor_release(a)
@@ -537,8 +544,13 @@ def microbench(ka, torch):
         ka.check(s)
         s, td, _ = ka.ka_bench_direct_chain([(ka.KA_STAGE_EMPTY, 0, 0, 0)], x, 1024, 5000)
         ka.check(s)
+        s, tt, _ = ka.ka_bench_direct_chain([(ka.KA_STAGE_EMPTY, 0, 0, 0)], x, 1024, 5000,
+                                            flags=ka.KA_BENCH_WAIT_TAG)
+        ka.check(s)
         out["empty_stage"] = {"actor_us": round(ta / 5000 * 1e6, 2), "direct_us": round(td / 5000 * 1e6, 2),
-                              "overhead_us": round((ta - td) / 5000 * 1e6, 2)}
+                              "overhead_us": round((ta - td) / 5000 * 1e6, 2),
+                              "direct_same_wait_us": round(tt / 5000 * 1e6, 2),
+                              "layer_us": round((ta - tt) / 5000 * 1e6, 2)}
         ka.ka_actor_release(empty)
         ka.ka_ref_release(ref)
         s, comp = ka.ka_spawn_stage(sysh, ka.KA_STAGE_COMPACT, ka.KA_PRED_LT, 1 << 31)
@@ -552,13 +564,18 @@ def microbench(ka, torch):
             ka.check(ka.ka_bench_request_loop(comp, m, 10, 1)[0])
             s, ta, ka_ = ka.ka_bench_request_loop(comp, m, iters, 1)
             ka.check(s)
-            s, td, kd = ka.ka_bench_direct_chain([(ka.KA_STAGE_COMPACT, ka.KA_PRED_LT, 1 << 31, 0)], x, n, iters)
+            spec = [(ka.KA_STAGE_COMPACT, ka.KA_PRED_LT, 1 << 31, 0)]
+            s, td, kd = ka.ka_bench_direct_chain(spec, x, n, iters)
+            ka.check(s)
+            s, tt, kt = ka.ka_bench_direct_chain(spec, x, n, iters, flags=ka.KA_BENCH_WAIT_TAG)
             ka.check(s)
             ka.ka_ref_release(r)
             out["overhead_vs_n"].append({"n": n, "actor_us": round(ta / iters * 1e6, 2),
                                          "direct_us": round(td / iters * 1e6, 2),
                                          "difference_us": round((ta - td) / iters * 1e6, 2),
-                                         "counts_match": int(ka_) == int(kd)})
+                                         "direct_same_wait_us": round(tt / iters * 1e6, 2),
+                                         "layer_us": round((ta - tt) / iters * 1e6, 2),
+                                         "counts_match": int(ka_) == int(kd) == int(kt)})
         ka.ka_actor_release(comp)
     finally:
         ka.ka_system_destroy(sysh, 1)

@@ -446,10 +446,17 @@ ka_status ka_actor_enable_graph(ka_actor *actor, int32_t enable);
 ka_status ka_bench_request_loop(ka_actor *actor, const ka_msg *msg, uint32_t iters, uint32_t inflight,
                                 double *seconds, uint64_t *last_count);
 /* The same stage chain launched directly (no actor layer) on `stream`,
- * iters times, each followed by a read-back of the result length and a
- * synchronisation. Buffers are allocated once; three untimed warm-up runs. */
+ * iters times, each followed by a read-back of the result length (a
+ * one-thread kernel storing it into host-mapped memory) and a wait. flags 0:
+ * the wait is cudaStreamSynchronize, as plain CUDA code would wait.
+ * KA_BENCH_WAIT_TAG: the wait is the one ka_receive uses (a completion tag
+ * that the same kernel stores last, polled in host memory; an event when the
+ * length is known on the host), so the two loops differ only by the actor
+ * layer. Buffers are allocated once; three untimed warm-up runs. */
+#define KA_BENCH_WAIT_TAG 1u
 ka_status ka_bench_direct_chain(const ka_stage_desc *stages, uint32_t n_stages, const uint32_t *d_in, uint64_t n,
-                                uint32_t iters, void *stream, double *seconds, uint64_t *last_count);
+                                uint32_t iters, void *stream, uint32_t flags, double *seconds,
+                                uint64_t *last_count);
 
 /* ------------------------------------------------------------------------ */
 /* Request loop with continuous batching (serving).                          */

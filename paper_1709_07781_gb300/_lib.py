@@ -176,7 +176,7 @@ _SIGS = {
     "ka_bench_request_loop": (ctypes.c_int32, [c_vp, ctypes.POINTER(ka_msg), ctypes.c_uint32, ctypes.c_uint32,
                                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
     "ka_bench_direct_chain": (ctypes.c_int32, [ctypes.POINTER(ka_stage_desc), ctypes.c_uint32, c_vp, ctypes.c_uint64,
-                                               ctypes.c_uint32, c_vp, ctypes.POINTER(ctypes.c_double),
+                                               ctypes.c_uint32, c_vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double),
                                                ctypes.POINTER(ctypes.c_uint64)]),
     "ka_serve_run": (ctypes.c_int32, [c_vp, ctypes.POINTER(ka_serve_request), ctypes.c_uint32,
                                       ctypes.POINTER(ka_serve_options), ctypes.POINTER(ka_serve_result),
@@ -553,9 +553,12 @@ def stage_descs(specs):
     return arr
 
 
-def ka_bench_direct_chain(specs, d_in, n: int, iters: int, stream=None):
+KA_BENCH_WAIT_TAG = 1
+
+
+def ka_bench_direct_chain(specs, d_in, n: int, iters: int, stream=None, flags: int = 0):
     arr = stage_descs(specs)
     sec, last = ctypes.c_double(0), ctypes.c_uint64(0)
-    s = lib.ka_bench_direct_chain(arr, len(specs), ptr(d_in), n, iters, stream_ptr(stream), ctypes.byref(sec),
-                                  ctypes.byref(last))
+    s = lib.ka_bench_direct_chain(arr, len(specs), ptr(d_in), n, iters, stream_ptr(stream), flags,
+                                  ctypes.byref(sec), ctypes.byref(last))
     return s, sec.value, last.value

@@ -62,8 +62,10 @@ ka_status ka_bench_request_loop(ka_actor *actor, const ka_msg *msg, uint32_t ite
 }
 
 ka_status ka_bench_direct_chain(const ka_stage_desc *stages, uint32_t n_stages, const uint32_t *d_in, uint64_t n,
-                                uint32_t iters, void *stream, double *seconds, uint64_t *last_count) {
+                                uint32_t iters, void *stream, uint32_t flags, double *seconds, uint64_t *last_count) {
     if (!stages || n_stages == 0 || !seconds || iters == 0 || n > 0xFFFFFFFFull) return KA_E_ARG;
+    if (flags & ~KA_BENCH_WAIT_TAG) return KA_E_ARG;
+    const bool wait_tag = (flags & KA_BENCH_WAIT_TAG) != 0;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // buffers: one output (+ count word) per stage output, allocated once
     std::vector<void *> allocs;
@@ -83,9 +85,12 @@ ka_status ka_bench_direct_chain(const ka_stage_desc *stages, uint32_t n_stages, 
     if (cudaMalloc(&ws, ws_bytes) != cudaSuccess) return KA_E_OOM;
     allocs.push_back(ws);
     s = ka_workspace_init(ws, ws_bytes, st);
-    uint32_t *pinned = nullptr, *pinned_dev = nullptr;  // host-mapped result word, as the actor layer uses
+    uint32_t *pinned = nullptr, *pinned_dev = nullptr;  // host-mapped result slot, as the actor layer uses
+    uint32_t seq = 0;                                     // completion tag of the current run
+    cudaEvent_t done = nullptr;
     if (s == KA_OK) s = cuda_status(cudaHostAlloc(&pinned, 16, cudaHostAllocMapped));
     if (s == KA_OK) s = cuda_status(cudaHostGetDevicePointer(reinterpret_cast<void **>(&pinned_dev), pinned, 0));
+    if (s == KA_OK && wait_tag) s = cuda_status(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
     // plan: per stage, its outputs (same arity conventions as the actor stages)
     std::vector<std::vector<Buf>> outs(n_stages);
     std::vector<Buf> cur;
@@ -185,13 +190,35 @@ ka_status ka_bench_direct_chain(const ka_stage_desc *stages, uint32_t n_stages, 
             c = o;
         }
         // the result length comes back to the host the way a receive delivers it
-        if (c[0].count) {
-            ka_status e = launch_publish(c[0].count, 1, 0, nullptr, pinned_dev, nullptr, st);
-            if (e != KA_OK) return e;
-        } else {
-            pinned[0] = uint32_t(c[0].n);
+        if (!wait_tag) {
+            if (c[0].count) {
+                ka_status e = launch_publish(c[0].count, 1, 0, nullptr, pinned_dev, nullptr, st);
+                if (e != KA_OK) return e;
+            } else {
+                pinned[0] = uint32_t(c[0].n);
+            }
+            return cuda_status(cudaStreamSynchronize(st));
         }
-        return cuda_status(cudaStreamSynchronize(st));
+        // KA_BENCH_WAIT_TAG: wait as ka_receive does, on the publish kernel's
+        // tag when there is a count word, else by polling an event
+        if (!c[0].count) {
+            pinned[0] = uint32_t(c[0].n);
+            ka_status e = cuda_status(cudaEventRecord(done, st));
+            cudaError_t q = cudaErrorNotReady;
+            while (e == KA_OK && (q = cudaEventQuery(done)) == cudaErrorNotReady) {
+            }
+            return e != KA_OK ? e : cuda_status(q);
+        }
+        seq = seq + 1 ? seq + 1 : 1;
+        ka_status e = launch_publish(c[0].count, 1, 0, nullptr, pinned_dev, nullptr, st, pinned_dev + 2, seq);
+        if (e != KA_OK) return e;
+        for (uint64_t spins = 1; __atomic_load_n(&pinned[2], __ATOMIC_ACQUIRE) != seq; ++spins) {
+            if ((spins & 0xFFFF) == 0) {  // a failed launch never stores the tag
+                const cudaError_t q = cudaStreamQuery(st);
+                if (q != cudaErrorNotReady && q != cudaSuccess) return cuda_status(q);
+            }
+        }
+        return KA_OK;
     };
     if (s == KA_OK) {
         for (int w = 0; w < 3 && s == KA_OK; ++w) s = run_once();
@@ -207,6 +234,7 @@ ka_status ka_bench_direct_chain(const ka_stage_desc *stages, uint32_t n_stages, 
         if (last_count) *last_count = pinned[0];
     }
     cudaStreamSynchronize(st);
+    if (done) cudaEventDestroy(done);
     if (pinned) cudaFreeHost(pinned);
     for (void *p : allocs) cudaFree(p);
     return s;

@@ -169,9 +169,12 @@ ka_status launch_copy_count(const uint32_t *n_ptr, uint64_t n, uint32_t *n_out, 
 // value `fixed` as one word) and, when err is given, the device error word,
 // stored straight into host-mapped pinned memory. One small launch stands in
 // for device-to-host copies, whose copy-engine round trip costs several
-// microseconds even for a single word.
+// microseconds even for a single word. With dst_tag, the value `tag` is
+// stored there last, after a system-scope fence: a host thread that reads
+// the tag knows that the words before it, and all work issued on the stream
+// before this launch, are complete (one block only).
 __global__ void k_publish(const uint32_t *src, uint32_t n, uint32_t fixed, const uint32_t *err, uint32_t *dst,
-                          uint32_t *dst_err) {
+                          uint32_t *dst_err, uint32_t *dst_tag, uint32_t tag) {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (!src) {
         if (t == 0) dst[0] = fixed;
@@ -179,13 +182,21 @@ __global__ void k_publish(const uint32_t *src, uint32_t n, uint32_t fixed, const
         for (uint32_t i = t; i < n; i += blockDim.x * gridDim.x) dst[i] = src[i];
     }
     if (err && t == 0) *dst_err = *err;
+    if (dst_tag) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence_system();
+            *reinterpret_cast<volatile uint32_t *>(dst_tag) = tag;
+        }
+    }
 }
 
 ka_status launch_publish(const uint32_t *src, uint32_t n, uint32_t fixed, const uint32_t *err, uint32_t *dst,
-                         uint32_t *dst_err, cudaStream_t stream) {
+                         uint32_t *dst_err, cudaStream_t stream, uint32_t *dst_tag, uint32_t tag) {
     if (!dst || (err && !dst_err)) return KA_E_ARG;
     const uint32_t blocks = src && n > 256 ? std::min<uint32_t>((n + 255) / 256, 16u) : 1u;
-    k_publish<<<blocks, 256, 0, stream>>>(src, n, fixed, err, dst, dst_err);
+    if (dst_tag && blocks != 1) return KA_E_ARG;
+    k_publish<<<blocks, 256, 0, stream>>>(src, n, fixed, err, dst, dst_err, dst_tag, tag);
     return cuda_status(cudaGetLastError());
 }
 

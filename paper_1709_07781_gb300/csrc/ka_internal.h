@@ -87,9 +87,10 @@ ka_status launch_scatter(const uint32_t *x, const uint32_t *flags, const uint32_
                          const uint32_t *n_ptr, uint32_t *out, uint32_t *count_out, cudaStream_t stream);
 ka_status launch_empty(cudaStream_t stream);
 // Stores n words of src (src null: the one word `fixed`) and, if err is not
-// null, *err into host-mapped pinned memory dst / dst_err.
+// null, *err into host-mapped pinned memory dst / dst_err; then, if dst_tag is
+// not null (n <= 256), `tag` into dst_tag after a system-scope fence.
 ka_status launch_publish(const uint32_t *src, uint32_t n, uint32_t fixed, const uint32_t *err, uint32_t *dst,
-                         uint32_t *dst_err, cudaStream_t stream);
+                         uint32_t *dst_err, cudaStream_t stream, uint32_t *dst_tag = nullptr, uint32_t tag = 0);
 ka_status launch_mandelbrot(uint32_t *out, uint32_t width, uint32_t height, float re_min, float im_min, float re_max,
                             float im_max, uint32_t max_iter, uint32_t *n_out, cudaStream_t stream);
 ka_status launch_generate(uint32_t *out, uint64_t n, uint64_t seed, uint32_t *n_out, cudaStream_t stream);

@@ -212,8 +212,10 @@ struct Request {
     std::vector<Ref *> result;
     uint64_t count = 0;
     ka_status status = KA_OK;
-    uint32_t *pinned_count = nullptr;  // host-mapped slot: length, device error word
+    uint32_t *pinned_count = nullptr;  // host-mapped slot: length, device error word, completion tag
     uint32_t *pinned_dev = nullptr;    // the same slot as the device addresses it
+    uint32_t seq = 0;                  // completion tag of the current use (changes every use)
+    bool tagged = false;               // the publish kernel stores `seq` when the stream gets there
     cudaEvent_t event = nullptr;
     std::mutex mu;
     std::condition_variable cv;
@@ -224,7 +226,7 @@ struct Request {
     std::atomic<int> holders{1};
     std::atomic<bool> recorded{false};  // event recorded after the last stage
     std::atomic<bool> claimed{false};   // a thread has taken on fulfilling the promise
-    std::atomic<bool> waiting{false};   // a receiver is polling the event
+    std::atomic<bool> waiting{false};   // a receiver is polling for completion
 };
 
 struct Msg : QNode {
@@ -303,6 +305,7 @@ HandleTable<Actor> g_actors;
 HandleTable<Request> g_requests;
 
 constexpr uint32_t kPinnedSlots = 65536;
+constexpr uint32_t kPinnedWords = 4;  // per slot: length, device error word, completion tag, unused
 
 // ---------------------------------------------------------------------------
 // References and the pool.
@@ -657,9 +660,15 @@ static Actor *process(System *s, Actor *a, Msg *m) {
     r->pinned_count[0] = first && !first->d_count ? uint32_t(first->n_host) : 0u;
     r->pinned_count[1] = 0;
     ka_status pub = KA_OK;
-    if ((first && first->d_count) || err)
+    r->tagged = false;
+    if ((first && first->d_count) || err) {
+        // the kernel stores a tag new to this use last: a receiver that sees
+        // it knows the result is complete without asking the driver
+        r->seq = r->seq + 1 ? r->seq + 1 : 1;
         pub = launch_publish(first ? first->d_count : nullptr, 1, r->pinned_count[0], err, r->pinned_dev,
-                             r->pinned_dev + 1, s->stream);
+                             r->pinned_dev + 1, s->stream, r->pinned_dev + 2, r->seq);
+        r->tagged = pub == KA_OK;
+    }
     cudaError_t rec = cudaSuccess;
     if (pub == KA_OK && !r->event) rec = cudaEventCreateWithFlags(&r->event, cudaEventDisableTiming);
     if (pub == KA_OK && rec == cudaSuccess) rec = cudaEventRecord(r->event, s->stream);
@@ -827,7 +836,7 @@ static uint32_t *take_pinned(System *s) {
     if (s->pin_free.empty()) return nullptr;
     const uint32_t i = s->pin_free.back();
     s->pin_free.pop_back();
-    return s->pinned + 2 * i;
+    return s->pinned + kPinnedWords * i;
 }
 
 // A request object: a recycled one when the system has one, else a new one
@@ -925,7 +934,7 @@ ka_status ka_system_create(const ka_config *cfg, ka_system **out) {
             cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
         }
     }
-    if (st == KA_OK) st = cuda_status(cudaHostAlloc(&s->pinned, size_t(kPinnedSlots) * 8, cudaHostAllocMapped));
+    if (st == KA_OK) st = cuda_status(cudaHostAlloc(&s->pinned, size_t(kPinnedSlots) * kPinnedWords * 4, cudaHostAllocMapped));
     if (st == KA_OK)
         st = cuda_status(cudaHostGetDevicePointer(reinterpret_cast<void **>(&s->pinned_dev), s->pinned, 0));
     if (st != KA_OK) {
@@ -1308,6 +1317,13 @@ ka_status ka_receive(ka_request_h *h, int64_t timeout_ns, ka_msg *out) {
                               : std::chrono::nanoseconds(int64_t(kReceiveSpinUs) * 1000);
         while (!r->done.load(std::memory_order_acquire) && std::chrono::steady_clock::now() - t0 < spin) {
             if (!r->recorded.load(std::memory_order_acquire) || r->claimed.load(std::memory_order_acquire)) continue;
+            if (r->tagged) {
+                // the publish kernel's tag: every stage has finished (a failed
+                // launch never stores it; the completion thread reports that)
+                if (__atomic_load_n(&r->pinned_count[2], __ATOMIC_ACQUIRE) != r->seq) continue;
+                if (!r->claimed.exchange(true, std::memory_order_acq_rel)) finalize(s, r, KA_OK);
+                continue;
+            }
             const cudaError_t q = cudaEventQuery(r->event);
             if (q == cudaErrorNotReady) continue;
             if (q != cudaSuccess) cudaGetLastError();

@@ -38,6 +38,26 @@ def test_every_declared_symbol_is_exported(ka):
     assert set(names) <= set(ka._lib.DECLARED), set(names) - set(ka._lib.DECLARED)
 
 
+def declared_arity():
+    """Parameter count of every function prototype in include/ka.h."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    text = re.sub(r"#[^\n]*", "", text)
+    out = {}
+    for m in re.finditer(r"\b(ka_[a-z0-9_]+)\s*\(([^()]*)\)\s*;", text):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_the_header(ka):
+    """Every ctypes prototype has as many arguments as the C declaration."""
+    arity = declared_arity()
+    assert len(arity) >= 40
+    wrong = {n: (len(ka._lib._SIGS[n][1]), k) for n, k in arity.items()
+             if n in ka._lib._SIGS and len(ka._lib._SIGS[n][1]) != k}
+    assert not wrong, wrong
+
+
 def test_strerror_and_version(ka):
     assert ka.ka_version() >= 100
     assert "timed out" in ka.ka_strerror(ka.KA_E_DEVICE_TIMEOUT)
@@ -141,3 +161,10 @@ def test_host_stream_scratch_size_and_refusals(ka):
     assert ka.ka_compact_host(x, 16, [], [], [], [], 1024, fake, b)[0] == ka.KA_E_ARG
     # n = 0 needs no device work: every count is 0
     assert ka.ka_compact_host(x, 0, [lt, lt], [5, 6], [0, 0], out * 2, 1024, fake, 1 << 40) == (0, [0, 0])
+
+
+def test_bench_direct_chain_refuses_unknown_flags(ka):
+    """Argument checks come before any CUDA call."""
+    spec = [(ka.KA_STAGE_EMPTY, 0, 0, 0)]
+    assert ka.ka_bench_direct_chain(spec, None, 16, 1, flags=2)[0] == ka.KA_E_ARG
+    assert ka.ka_bench_direct_chain(spec, None, 16, 0, flags=ka.KA_BENCH_WAIT_TAG)[0] == ka.KA_E_ARG

@@ -533,3 +533,24 @@ def test_receive_time_out_bounds_the_wait(ka, system):
     for j in range(m.n_refs):
         ka.ka_ref_release(m.refs[j])
     ka.ka_actor_release(a)
+
+
+@pytest.mark.parametrize("flags", [0, 1])
+def test_bench_loops_count_like_the_oracle(ka, system, flags):
+    """The native timing loops (direct chain, with either wait, and the
+    request loop) compute the same result length as the oracle."""
+    n = (1 << 18) + 3
+    x = ki.uniform_u32(21, n)
+    d_x = to_dev(x)
+    spec = [(ka.KA_STAGE_COMPACT, ka.KA_PRED_LT, ki.threshold_for(0.4), 0)]
+    s, sec, k_direct = ka.ka_bench_direct_chain(spec, d_x, n, 5, flags=flags)
+    assert s == 0 and sec > 0
+    comp = spawn(ka, system, ka.KA_STAGE_COMPACT, ka.KA_PRED_LT, ki.threshold_for(0.4))
+    s, rx = ka.ka_ref_wrap(system, d_x, n, n)
+    assert s == 0
+    s, sec, k_actor = ka.ka_bench_request_loop(comp, ka.make_msg([rx]), 5, 1)
+    assert s == 0
+    _, k = oracle.compact(x, "lt", ki.threshold_for(0.4))
+    assert k_direct == k_actor == k
+    ka.ka_ref_release(rx)
+    ka.ka_actor_release(comp)
