@@ -72,6 +72,9 @@ typedef int32_t ka_status;
 const char *ka_strerror(ka_status s);
 /* Library version: major * 100 + minor. */
 int32_t ka_version(void);
+/* The cudaError_t value behind the last KA_E_CUDA that a call made on this
+ * thread returned (0 if none has). */
+int32_t ka_last_cuda_error(void);
 
 /* ------------------------------------------------------------------------ */
 /* Predicates: which entries a compaction keeps (Sec. 4.1 removes entries    */

@@ -114,6 +114,7 @@ MONITOR_FN = ctypes.CFUNCTYPE(None, c_vp, ctypes.c_int32)
 _SIGS = {
     "ka_strerror": (ctypes.c_char_p, [ctypes.c_int32]),
     "ka_version": (ctypes.c_int32, []),
+    "ka_last_cuda_error": (ctypes.c_int32, []),
     "ka_workspace_size": (ctypes.c_int32, [ctypes.c_uint64, ctypes.POINTER(ka_tile), ctypes.POINTER(ctypes.c_uint64)]),
     "ka_workspace_init": (ctypes.c_int32, [c_vp, ctypes.c_uint64, c_vp]),
     "ka_workspace_status": (ctypes.c_int32, [c_vp, c_vp, ctypes.POINTER(ctypes.c_int32)]),
@@ -231,6 +232,10 @@ def ka_strerror(status: int) -> str:
 
 def ka_version() -> int:
     return lib.ka_version()
+
+
+def ka_last_cuda_error() -> int:
+    return lib.ka_last_cuda_error()
 
 
 def ka_workspace_size(capacity: int, tile=None):

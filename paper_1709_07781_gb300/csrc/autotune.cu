@@ -198,7 +198,10 @@ ka_status autotune_batch(uint64_t total, const char *cache_path, ka_tile *best, 
                 win = t;
             }
         }
-        if (win.block == 0) s = KA_E_CUDA;
+        if (win.block == 0) {  // no shape ran
+            const cudaError_t e = cudaGetLastError();
+            s = cuda_status(e != cudaSuccess ? e : cudaErrorUnknown);
+        }
     }
     cudaStreamSynchronize(st);
     if (in) cudaFree(in);
@@ -272,7 +275,10 @@ ka_status ka_autotune(int32_t kernel, uint64_t n, const char *cache_path, ka_til
                 win = t;
             }
         }
-        if (win.block == 0) s = KA_E_CUDA;
+        if (win.block == 0) {  // no shape ran
+            const cudaError_t e = cudaGetLastError();
+            s = cuda_status(e != cudaSuccess ? e : cudaErrorUnknown);
+        }
     }
     cudaStreamSynchronize(st);
     if (in) cudaFree(in);

@@ -6,6 +6,7 @@
 
 namespace ka {
 
+// The CUDA error behind the last KA_E_CUDA on this thread (ka_last_cuda_error).
 static thread_local int g_last_cuda_error = 0;
 
 ka_status cuda_status(cudaError_t e) {
@@ -99,6 +100,8 @@ const char *ka_strerror(ka_status s) {
 }
 
 int32_t ka_version(void) { return 100; }
+
+int32_t ka_last_cuda_error(void) { return g_last_cuda_error; }
 
 ka_status ka_workspace_size(uint64_t capacity, const ka_tile *tile, uint64_t *bytes) {
     if (!bytes) return KA_E_ARG;

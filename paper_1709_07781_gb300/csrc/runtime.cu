@@ -591,12 +591,11 @@ static ka_status run_stage(System *s, const StageSpec &sp, Msg *m, Ref **outs, i
         return e;
     }
     case KA_STAGE_PREPARE: {
-        Ref *b = m->refs[1];
+        const Ref *b = m->refs[1];
         Ref *y;
         if ((e = new_owned_ref(s, 2 * x->capacity, &y)) != KA_OK) return e;
-        (void)b;
-        e = launch_prepare_index(static_cast<const uint32_t *>(x->ptr), static_cast<const uint32_t *>(m->refs[1]->ptr),
-                                 n, n_ptr, static_cast<uint32_t *>(y->ptr), y->d_count, st);
+        e = launch_prepare_index(static_cast<const uint32_t *>(x->ptr), static_cast<const uint32_t *>(b->ptr), n,
+                                 n_ptr, static_cast<uint32_t *>(y->ptr), y->d_count, st);
         outs[(*n_outs)++] = y;
         return e;
     }
@@ -910,10 +909,10 @@ ka_status ka_system_create(const ka_config *cfg, ka_system **out) {
     s->device = cfg ? cfg->device : 0;
     s->debug = cfg && cfg->debug;
     s->budget = (cfg && cfg->budget_bytes) ? cfg->budget_bytes : (64ull << 30);
-    if (cudaSetDevice(s->device) != cudaSuccess) {
+    if (const cudaError_t e = cudaSetDevice(s->device); e != cudaSuccess) {
         cudaGetLastError();
         delete s;
-        return KA_E_CUDA;
+        return cuda_status(e);
     }
     ka_status st = KA_OK;
     if (cfg && cfg->stream) {

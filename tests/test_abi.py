@@ -168,3 +168,14 @@ def test_bench_direct_chain_refuses_unknown_flags(ka):
     spec = [(ka.KA_STAGE_EMPTY, 0, 0, 0)]
     assert ka.ka_bench_direct_chain(spec, None, 16, 1, flags=2)[0] == ka.KA_E_ARG
     assert ka.ka_bench_direct_chain(spec, None, 16, 0, flags=ka.KA_BENCH_WAIT_TAG)[0] == ka.KA_E_ARG
+
+
+def test_last_cuda_error_names_the_failure(ka):
+    """Without a GPU, a call that needs the device returns KA_E_CUDA, and
+    ka_last_cuda_error gives the CUDA error behind it."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    s, _ = ka.ka_system_create(0)
+    assert s == ka.KA_E_CUDA
+    assert ka.ka_last_cuda_error() != 0
