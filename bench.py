@@ -445,7 +445,9 @@ def actor_overhead(ka, torch):
     (N = 2^26: hash, keep top bits < 8, keep popc odd, keep % 3 != 0).
     Two direct loops: one waits with cudaStreamSynchronize (plain CUDA code,
     `overhead_pct`), the other with the wait the receiver uses, a completion
-    tag polled in host memory (`layer_overhead_pct`: the actor layer alone)."""
+    tag polled in host memory (`layer_overhead_pct`: the actor layer alone).
+    The three loops run in three interleaved rounds; each figure is the
+    median round."""
     import ka_inputs as ki
     P = ka.PRED
     cases = [
@@ -482,17 +484,26 @@ def actor_overhead(ka, torch):
             ka.check(s)
             msg = ka.make_msg(refs=[ref])
             ka.check(ka.ka_bench_request_loop(pipe, msg, 20, 1)[0])  # warm-up (pool, autotune table)
-            s, t_actor, k_actor = ka.ka_bench_request_loop(pipe, msg, iters, 1)
-            ka.check(s)
-            s, t_direct, k_direct = ka.ka_bench_direct_chain(specs, x, n, iters)
-            ka.check(s)
-            s, t_tag, k_tag = ka.ka_bench_direct_chain(specs, x, n, iters, flags=ka.KA_BENCH_WAIT_TAG)
-            ka.check(s)
-            us_a, us_d, us_t = t_actor / iters * 1e6, t_direct / iters * 1e6, t_tag / iters * 1e6
-            out.append({"pipeline": name, "n": n, "iters": iters, "actor_us": round(us_a, 2),
+            # three interleaved rounds of the three loops; medians over rounds
+            per = max(iters // 3, 1)
+            ra, rd, rt = [], [], []
+            for _ in range(3):
+                s, t_actor, k_actor = ka.ka_bench_request_loop(pipe, msg, per, 1)
+                ka.check(s)
+                s, t_direct, k_direct = ka.ka_bench_direct_chain(specs, x, n, per)
+                ka.check(s)
+                s, t_tag, k_tag = ka.ka_bench_direct_chain(specs, x, n, per, flags=ka.KA_BENCH_WAIT_TAG)
+                ka.check(s)
+                ra.append(t_actor / per * 1e6)
+                rd.append(t_direct / per * 1e6)
+                rt.append(t_tag / per * 1e6)
+            us_a, us_d, us_t = sorted(ra)[1], sorted(rd)[1], sorted(rt)[1]
+            out.append({"pipeline": name, "n": n, "iters": 3 * per, "actor_us": round(us_a, 2),
                         "direct_us": round(us_d, 2), "overhead_pct": round(100.0 * (us_a / us_d - 1.0), 2),
                         "direct_same_wait_us": round(us_t, 2),
                         "layer_overhead_pct": round(100.0 * (us_a / us_t - 1.0), 2),
+                        "rounds_us": {"actor": [round(v, 2) for v in ra], "direct": [round(v, 2) for v in rd],
+                                      "direct_same_wait": [round(v, 2) for v in rt]},
                         "actor_elements/s": n / (us_a * 1e-6), "count": int(k_actor),
                         "counts_match": int(k_actor) == int(k_direct) == int(k_tag)})
             ka.ka_ref_release(ref)
