@@ -58,10 +58,11 @@ def parse_args():
     p.add_argument("--tile", default="", help="block,ipt: fix the tile shape instead of autotuning it")
     p.add_argument("--clock-interval-ms", type=int, default=100,
                    help="nvidia-smi sampling interval during the timed region (0: do not sample)")
-    p.add_argument("--only", choices=["", "scan", "batch", "serve"], default="",
-                   help="time one part alone: the exclusive scan of --n flags, or the 4096-instance batch "
-                        "(W warm-up and K timed launches, for profiling); or the serving comparison at "
-                        "20 000 requests/s for --serve-duration seconds")
+    p.add_argument("--only", choices=["", "scan", "batch", "three_phase", "mandelbrot", "serve"], default="",
+                   help="time one part alone: the exclusive scan of --n flags, the 4096-instance batch, the "
+                        "three-phase compaction of --n entries (keep x < 2^31), or the 16000 x 16000 "
+                        "Mandelbrot image at 100 steps (W warm-up and K timed launches, for profiling); or "
+                        "the serving comparison at 20 000 requests/s for --serve-duration seconds")
     p.add_argument("--serve-duration", type=float, default=1.0,
                    help="seconds of the 20 000 requests/s serving trace (the configuration's full run is 60)")
     return p.parse_args()
@@ -942,6 +943,29 @@ def run_only(args):
         def launch():
             ka.check(ka.ka_exclusive_scan(f, N, None, o, tot, ws, wsb, tile, st.cuda_stream))
         units, bytes_ = N, 8.0 * N
+    elif args.only == "three_phase":
+        N = args.n
+        x = torch.empty(N, dtype=torch.int32, device="cuda")
+        ka.check(ka.ka_generate(x, N, SEED, st.cuda_stream))
+        y, tot = torch.empty_like(x), torch.zeros(4, dtype=torch.int32, device="cuda")
+        s, wsb = ka.ka_three_phase_workspace_size(N)
+        ka.check(s)
+        ws_t = torch.empty(wsb + 256, dtype=torch.uint8, device="cuda")
+        ws = (ws_t.data_ptr() + 255) // 256 * 256
+        ka.check(ka.ka_workspace_init(ws, wsb, st.cuda_stream))
+
+        def launch():
+            ka.check(ka.ka_compact_three_phase(x, N, None, ka.KA_PRED_LT, 1 << 31, 0, y, tot, ws, wsb,
+                                               st.cuda_stream))
+        units, bytes_ = N, None
+        cnt = tot[:1]
+    elif args.only == "mandelbrot":
+        w = h = 16000
+        img = torch.empty(w * h, dtype=torch.int32, device="cuda")
+
+        def launch():
+            ka.check(ka.ka_mandelbrot(img, w, h, -0.5, -0.7375, 0.1, -0.1375, 100, st.cuda_stream))
+        units, bytes_ = w * h, 4.0 * w * h
     else:
         spec = ki.config_batch()
         m = len(spec.n)
@@ -978,12 +1002,15 @@ def run_only(args):
     e1.record(st)
     torch.cuda.synchronize()
     us = e0.elapsed_time(e1) * 1000.0 / K
-    if bytes_ is None:
-        bytes_ = 4.0 * units + 4.0 * float(cnt.cpu().numpy().view(np.uint32).astype(np.int64).sum())
+    if bytes_ is None:  # compactions: input read once (twice for the three-phase method) + kept entries
+        reads = 8.0 if args.only == "three_phase" else 4.0
+        bytes_ = reads * units + 4.0 * float(cnt.cpu().numpy().view(np.uint32).astype(np.int64).sum())
     peak, peak_kind = measured_peak_gbs()
-    print(json.dumps({"only": args.only, "tile": list(tile) if tile else None, "units": units, "us": round(us, 2),
-                      "GB/s": round(bytes_ / us / 1e3, 1), "frac": round(bytes_ / us / 1e3 / peak, 4),
-                      "peak_kind": peak_kind}), flush=True)
+    line = {"only": args.only, "tile": list(tile) if tile else None, "units": units, "us": round(us, 2),
+            "GB/s": round(bytes_ / us / 1e3, 1), "frac": round(bytes_ / us / 1e3 / peak, 4), "peak_kind": peak_kind}
+    if args.only == "mandelbrot":
+        line["note"] = "image bytes only: the kernel is bound by FP32 arithmetic, not HBM"
+    print(json.dumps(line), flush=True)
 
 
 def run_serve_only(args):
