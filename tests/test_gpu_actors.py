@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 import ka_inputs as ki  # noqa: E402
 import oracle  # noqa: E402
-from gpu_util import empty, stream, to_dev, to_host  # noqa: E402
+from gpu_util import empty, stream, to_dev  # noqa: E402
 
 
 @pytest.fixture(scope="module")
