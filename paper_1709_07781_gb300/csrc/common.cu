@@ -15,6 +15,11 @@ ka_status cuda_status(cudaError_t e) {
     return KA_E_CUDA;
 }
 
+int current_device() {
+    int dev = -1;
+    return cudaGetDevice(&dev) == cudaSuccess ? dev : -1;
+}
+
 const DeviceInfo &device_info() {
     static std::mutex mu;
     static DeviceInfo cache[64];

@@ -75,7 +75,6 @@ struct HostCtx {
     std::mutex mu;
 };
 
-constexpr int kMaxDevices = 64;
 HostCtx g_host[kMaxDevices];
 
 ka_status host_ctx_setup(HostCtx &c) {

@@ -138,12 +138,12 @@ __global__ void __launch_bounds__(BLOCK) k_compact_batch(const BatchArgs a) {
 
 template <int BLOCK, int IPT>
 static ka_status launch_batch_shape(const BatchArgs &a, uint32_t grid, cudaStream_t stream) {
-    static int occupancy = 0;
-    if (occupancy == 0) {
+    static PerDeviceInt occ_cache;
+    const int occupancy = per_device_value(occ_cache, current_device(), [] {
         int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_compact_batch<BLOCK, IPT>, BLOCK, 0);
-        occupancy = occ > 0 ? occ : 1;
-    }
+        return occ > 0 ? occ : 1;
+    });
     const uint64_t resident = uint64_t(device_info().sm_count) * occupancy;
     uint64_t g = grid ? grid : resident;
     if (g > resident) g = resident;  // every block resident: tickets need no more

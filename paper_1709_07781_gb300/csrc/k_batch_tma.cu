@@ -289,16 +289,18 @@ ka_status launch_batch_tma_shape(const BatchArgs &a, uint32_t grid, cudaStream_t
     constexpr int BLOCK = (CWW + 2) * 32, T = CWW * kSeg;
     const size_t smem = size_t(S) * T * 4;
     auto kern = k_batch_tma<CWW, S, LAG, MAXG, MINB>;
-    static int resident = 0;
-    if (resident == 0) {
+    // per device: the shared-memory attribute holds for the current device only
+    static PerDeviceInt grid_cache;
+    const int resident = per_device_value(grid_cache, current_device(), [&] {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
-            return cuda_status(cudaGetLastError());
+            return -1;
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BLOCK, smem) != cudaSuccess || occ < 1)
-            return cuda_status(cudaGetLastError());
+            return -1;
         const int g = device_info().sm_count * occ;
-        resident = g > MAXG ? MAXG : g;
-    }
+        return g > MAXG ? MAXG : g;
+    });
+    if (resident <= 0) return launch_setup_error();
     const uint32_t g = grid && grid < uint32_t(resident) ? grid : uint32_t(resident);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(g);

@@ -73,12 +73,12 @@ __global__ void __launch_bounds__(BLOCK) k_compact_fused(const CompactArgs a) {
 template <int BLOCK, int IPT>
 static ka_status launch_shape(const CompactArgs &a, uint64_t cap, cudaStream_t stream) {
     constexpr int T = BLOCK * IPT;
-    static int occupancy = 0;
-    if (occupancy == 0) {
+    static PerDeviceInt occ_cache;
+    const int occupancy = per_device_value(occ_cache, current_device(), [] {
         int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_compact_fused<BLOCK, IPT>, BLOCK, 0);
-        occupancy = occ > 0 ? occ : 1;
-    }
+        return occ > 0 ? occ : 1;
+    });
     uint64_t grid = (cap + T - 1) / T;
     const uint64_t resident = uint64_t(device_info().sm_count) * occupancy;
     if (grid > resident) grid = resident;

@@ -27,7 +27,6 @@ constexpr uint64_t kStaticScratchBytes = kWsHeaderBytes + ((2 * kStaticTiles * k
 // comes from cudaGetSymbolAddress, once per device, with that device current.
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 void *g_static_ptr[kMaxDevices] = {};
 

@@ -99,12 +99,12 @@ ka_status launch_scatter(const uint32_t *x, const uint32_t *flags, const uint32_
     a.vec_ok = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(flags) |
                  reinterpret_cast<uintptr_t>(offsets)) & 15u) == 0 ? 1u : 0u;
     constexpr int T = kScatterBlock * kScatterIpt;
-    static int occupancy = 0;
-    if (occupancy == 0) {
+    static PerDeviceInt occ_cache;
+    const int occupancy = per_device_value(occ_cache, current_device(), [] {
         int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_scatter, kScatterBlock, 0);
-        occupancy = occ > 0 ? occ : 1;
-    }
+        return occ > 0 ? occ : 1;
+    });
     uint64_t grid = (n + T - 1) / T;
     const uint64_t resident = uint64_t(device_info().sm_count) * occupancy;
     if (grid > resident) grid = resident;

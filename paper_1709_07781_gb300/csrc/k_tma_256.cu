@@ -6,7 +6,7 @@ namespace ka {
 namespace tma {
 
 ka_status launch_tma_256(const TmaArgs &a, bool scan, int32_t pk, uint64_t cap, cudaStream_t stream) {
-    return launch_tma_config<8, 4, 2, 480, 3>(a, scan, pk, cap, stream);
+    return launch_tma_config<8, 4, 2, 480, 3, 4, 1>(a, scan, pk, cap, stream);
 }
 
 }  // namespace tma

@@ -6,7 +6,7 @@ namespace ka {
 namespace tma {
 
 ka_status launch_tma_512(const TmaArgs &a, bool scan, int32_t pk, uint64_t cap, cudaStream_t stream) {
-    return launch_tma_config<16, 3, 2, 320, 2>(a, scan, pk, cap, stream);
+    return launch_tma_config<16, 3, 2, 320, 2, 4, 1>(a, scan, pk, cap, stream);
 }
 
 }  // namespace tma

@@ -1,6 +1,7 @@
 // Internal host-side declarations of libka (not part of the C ABI).
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -16,6 +17,33 @@ struct DeviceInfo {
     int max_smem_optin = 0;
 };
 const DeviceInfo &device_info();
+
+// A launch quantity (occupancy, resident grid size) cached per device
+// ordinal: devices differ in SM count and resident slots, and a function
+// attribute set with cudaFuncSetAttribute holds for the current device only.
+constexpr int kMaxDevices = 64;
+struct PerDeviceInt {
+    std::atomic<int> slot[kMaxDevices];  // 0: not computed yet (static storage starts at zero)
+};
+// Ordinal of the calling thread's current device (-1 on error).
+int current_device();
+// The value for device `dev`: the cached one, else compute(), cached when it
+// is positive (a value <= 0 reports an error and is not cached). Threads that
+// race on a first use both compute the same value.
+template <class F>
+int per_device_value(PerDeviceInt &cache, int dev, F &&compute) {
+    if (dev < 0 || dev >= kMaxDevices) return compute();
+    const int v = cache.slot[dev].load(std::memory_order_acquire);
+    if (v > 0) return v;
+    const int w = compute();
+    if (w > 0) cache.slot[dev].store(w, std::memory_order_release);
+    return w;
+}
+
+// Status of a launch whose set-up (function attribute, occupancy) failed: the
+// CUDA error behind it, or KA_E_UNSUPPORTED when the kernel cannot be
+// resident on this device at all.
+inline ka_status launch_setup_error();
 
 // cudaError_t -> ka_status (records the CUDA error for ka_strerror detail).
 ka_status cuda_status(cudaError_t e);
@@ -106,5 +134,10 @@ ka_status launch_copy_count(const uint32_t *n_ptr, uint64_t n, uint32_t *n_out, 
 ka_status check_workspace(const void *ws, uint64_t ws_bytes, uint64_t tiles_needed);
 
 constexpr uint32_t kHashMul = 2654435761u;
+
+inline ka_status launch_setup_error() {
+    const cudaError_t e = cudaGetLastError();
+    return e != cudaSuccess ? cuda_status(e) : KA_E_UNSUPPORTED;
+}
 
 }  // namespace ka

@@ -124,6 +124,58 @@ def test_tma_unaligned_input(ka, shape, in_off):
     assert np.array_equal(to_host(d)[:in_off], x[:in_off])
 
 
+def varied_segments(seed, n, seg=512):
+    """Uniform entries rewritten so that `x < 2^31` keeps them with a
+    selectivity that changes every `seg` entries (0, 2, 6.25, 8, 50 or 100 %):
+    the kept counts of one tile's 512-entry segments then fall on both sides
+    of the 32 entries a segment may keep and still be spilled, and each tile
+    mixes spilled and held segments."""
+    u = ki.uniform_u32(seed, n)
+    rng = np.random.default_rng(seed)
+    frac = np.array([0.0, 0.02, 0.0625, 0.08, 0.5, 1.0])[rng.integers(0, 6, size=(n + seg - 1) // seg)]
+    keep = (u.astype(np.float64) / 2.0**32) < np.repeat(frac, seg)[:n]
+    return np.where(keep, u >> np.uint32(1), u | np.uint32(0x80000000)).astype(np.uint32)
+
+
+@pytest.mark.parametrize("shape", TMA_SHAPES)
+@pytest.mark.parametrize("s", [0.001, 0.01, 0.03, 0.0625, 0.08])
+def test_tma_low_selectivity(ka, shape, s):
+    """Selectivities whose segments keep at most 32 entries (compacted into
+    the warps' spill rings and written out by the look-back warp), around 32
+    (both kinds in one tile) and just above it."""
+    T = shape[0] * shape[1]
+    for n in [5, T - 1, 3 * T + 5, (1 << 22) + 12345]:
+        x = ki.uniform_u32(int(s * 1e4) + n, n)
+        out, k = compact(ka, to_dev(x), n, "lt", ki.threshold_for(s), shape)
+        y, ek = oracle.compact(x, "lt", ki.threshold_for(s))
+        assert k == ek and np.array_equal(to_host(out, k), y), (n, s)
+        assert np.all(to_host(out)[k:n + 16] == SENTINEL)
+
+
+@pytest.mark.parametrize("shape", TMA_SHAPES)
+@pytest.mark.parametrize("in_off", [0, 1, 2, 3])
+def test_tma_mixed_segments(ka, shape, in_off):
+    """Tiles whose segments keep anywhere from none to all of their entries,
+    at every input offset, with an unaligned output, in place, and with a live
+    length from a device word."""
+    n = (1 << 22) + 777
+    x = varied_segments(400 + in_off, n + in_off)
+    d = to_dev(x, pad=16)
+    y, ek = oracle.compact(x[in_off:], "lt", 1 << 31)
+    base = empty(n + 32)
+    out, k = compact(ka, d[in_off:], n, "lt", 1 << 31, shape, out=base[1 + in_off:])
+    assert k == ek and np.array_equal(to_host(base[1 + in_off:], k), y)
+    assert np.all(to_host(base)[:1 + in_off] == SENTINEL) and np.all(to_host(base)[1 + in_off + k:] == SENTINEL)
+    live = n - 4321
+    out, k = compact(ka, d[in_off:], n, "lt", 1 << 31, shape, d_n=to_dev(np.array([live], dtype=np.uint32)))
+    yl, el = oracle.compact(x[in_off:in_off + live], "lt", 1 << 31)
+    assert k == el and np.array_equal(to_host(out, k), yl)
+    out, k = compact(ka, d[in_off:], n, "lt", 1 << 31, shape, out=d[in_off:])
+    assert k == ek and np.array_equal(to_host(d)[in_off:in_off + k], y)
+    assert np.array_equal(to_host(d)[:in_off], x[:in_off]) and np.array_equal(to_host(d)[in_off + k:n + in_off],
+                                                                             x[in_off + k:])
+
+
 @pytest.mark.parametrize("shape", TMA_SHAPES)
 def test_tma_workspace_reuse_and_shape_mix(ka, shape):
     ws = Workspace(ka, 1 << 22, (128, 4))  # sized for the smallest tile: fits every shape
