@@ -186,12 +186,26 @@ ka_status ka_compact(const uint32_t *d_in, uint64_t n, const uint32_t *d_n, int3
  * Every call on a device shares the one array, which keeps what the previous
  * call left in it; calls whose kernels overlap on the GPU (unordered streams)
  * race and give undefined results, so order them (one stream, or events).
- * A device-side look-back timeout is recorded only inside the shared array,
- * which no entry point reads. */
+ * A device-side failure (a look-back that gave up after its bounded wait) is
+ * recorded in the shared array's header, like ka_compact's in its workspace:
+ * read it with ka_workspace_status on the address ka_compact_static_workspace
+ * returns; the count and output of a call after which it reports an error
+ * are undefined. The error stays recorded (first error wins) until
+ * ka_workspace_init is run on that address. */
 #define KA_STATIC_MAX_N (1ull << 24)
 ka_status ka_compact_static(const uint32_t *d_in, uint64_t n, const uint32_t *d_n, int32_t pred,
                             uint32_t param, uint32_t xform, uint32_t *d_out, uint32_t *d_count,
                             const ka_tile *tile, void *stream);
+/* The shared array of the current device, as a workspace: *d_ws its device
+ * address, *bytes its size. Allocates nothing; sets the array up as the first
+ * ka_compact_static call does (same rule on stream capture) if no call has
+ * yet. With it a caller checks a call (ka_workspace_status: synchronises
+ * `stream`, copies the 256-byte header into host memory), clears a recorded
+ * error (ka_workspace_init on `stream`, ordered after the calls), or sets the
+ * spin limit (ka_workspace_set_spin_limit). Errors: KA_E_ARG (null output),
+ * KA_E_UNSUPPORTED (first use during a capture, or device ordinal >= 64),
+ * KA_E_CUDA. The paper has no counterpart. */
+ka_status ka_compact_static_workspace(void *stream, void **d_ws, uint64_t *bytes);
 
 /* Three-phase compaction (Sec. 4.1: count, prefix sum, move, after Billeter
  * et al.): per-segment kept counts (segments of 512 entries, one warp's
@@ -425,6 +439,12 @@ ka_status ka_receive(ka_request_h *req, int64_t timeout_ns, ka_msg *out);
  * the library's canonicalisation, e.g. the division-free modulus test); lets
  * a CPU test compare it with the plain definition. *keep = 0 or 1. */
 ka_status ka_debug_pred_keep(int32_t pred, uint32_t param, uint32_t x, int32_t *keep);
+/* Test hook for the per-device launch caches (no GPU needed): looks up
+ * devices[i] in order in a fresh cache whose computation for lookup i
+ * returns values[i], and writes what each lookup returned to out[i]. A value
+ * is cached per device ordinal only when positive, and only for ordinals
+ * below 64. */
+ka_status ka_debug_device_cache(const int32_t *devices, const int32_t *values, uint32_t n, int32_t *out);
 
 /* Test hooks (host-side fault injection; no GPU fault involved). */
 ka_status ka_debug_fail_stage(ka_actor *stage_actor, int32_t fail_after);  /* -1: off */
@@ -433,10 +453,6 @@ typedef void (*ka_monitor_fn)(void *user, ka_status reason);
 /* Called once from the system's threads when the dispatcher dies (link/monitor
  * notification, Sec. 2.1). */
 ka_status ka_system_monitor(ka_system *sys, ka_monitor_fn fn, void *user);
-
-/* Capture the composite's launch sequence for messages of the given input
- * capacity into a CUDA graph, replayed for later requests of that shape. */
-ka_status ka_actor_enable_graph(ka_actor *actor, int32_t enable);
 
 /* ------------------------------------------------------------------------ */
 /* Native timing loops for the actor-overhead measurement (Sec. 5.2-5.3: an   */
@@ -455,7 +471,9 @@ ka_status ka_bench_request_loop(ka_actor *actor, const ka_msg *msg, uint32_t ite
  * KA_BENCH_WAIT_TAG: the wait is the one ka_receive uses (a completion tag
  * that the same kernel stores last, polled in host memory; an event when the
  * length is known on the host), so the two loops differ only by the actor
- * layer. Buffers are allocated once; three untimed warm-up runs. */
+ * layer. Buffers are allocated once; three untimed warm-up runs. A first
+ * stage KA_STAGE_PREPARE (the interleave of fuseFillsLiterals) reads its two
+ * inputs from d_in: n chunk ids, then n literals. */
 #define KA_BENCH_WAIT_TAG 1u
 ka_status ka_bench_direct_chain(const ka_stage_desc *stages, uint32_t n_stages, const uint32_t *d_in, uint64_t n,
                                 uint32_t iters, void *stream, uint32_t flags, double *seconds,
@@ -513,6 +531,13 @@ typedef struct ka_serve_stats {
     uint32_t rejected;           /* requests larger than the whole budget            */
     uint64_t graph_launches;     /* ticks issued as one CUDA graph launch (mode 0)   */
     uint64_t lone_ticks;         /* ticks of one request issued as plain launches    */
+    /* Host-side timing of the serving loop, to locate stalls: its longest step
+     * (taking arrivals, polling completions, issuing work), the number of steps
+     * longer than 1 ms, and the longest single admission allocation, buffer
+     * release, issue (launches or graph launch) and completion poll. */
+    double max_step_s;
+    uint64_t slow_steps;
+    double max_alloc_s, max_free_s, max_issue_s, max_poll_s;
 } ka_serve_stats;
 
 ka_status ka_serve_run(ka_system *sys, const ka_serve_request *reqs, uint32_t n_reqs,

@@ -105,7 +105,10 @@ class ka_serve_stats(ctypes.Structure):
     _fields_ = [("wall_s", ctypes.c_double), ("elements", ctypes.c_uint64), ("launches", ctypes.c_uint64),
                 ("iterations", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
                 ("max_inflight_seen", ctypes.c_uint32), ("rejected", ctypes.c_uint32),
-                ("graph_launches", ctypes.c_uint64), ("lone_ticks", ctypes.c_uint64)]
+                ("graph_launches", ctypes.c_uint64), ("lone_ticks", ctypes.c_uint64),
+                ("max_step_s", ctypes.c_double), ("slow_steps", ctypes.c_uint64),
+                ("max_alloc_s", ctypes.c_double), ("max_free_s", ctypes.c_double),
+                ("max_issue_s", ctypes.c_double), ("max_poll_s", ctypes.c_double)]
 
 
 MONITOR_FN = ctypes.CFUNCTYPE(None, c_vp, ctypes.c_int32)
@@ -129,6 +132,7 @@ _SIGS = {
                                     c_vp, c_vp, c_vp, ctypes.c_uint64, ctypes.POINTER(ka_tile), c_vp]),
     "ka_compact_static": (ctypes.c_int32, [c_vp, ctypes.c_uint64, c_vp, ctypes.c_int32, ctypes.c_uint32,
                                            ctypes.c_uint32, c_vp, c_vp, ctypes.POINTER(ka_tile), c_vp]),
+    "ka_compact_static_workspace": (ctypes.c_int32, [c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(ctypes.c_uint64)]),
     "ka_three_phase_workspace_size": (ctypes.c_int32, [ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
     "ka_compact_three_phase": (ctypes.c_int32, [c_vp, ctypes.c_uint64, c_vp, ctypes.c_int32, ctypes.c_uint32,
                                                 ctypes.c_uint32, c_vp, c_vp, c_vp, ctypes.c_uint64, c_vp]),
@@ -168,12 +172,13 @@ _SIGS = {
     "ka_actor_release": (ctypes.c_int32, [c_vp]),
     "ka_request": (ctypes.c_int32, [c_vp, ctypes.POINTER(ka_msg), ctypes.POINTER(c_vp)]),
     "ka_receive": (ctypes.c_int32, [c_vp, ctypes.c_int64, ctypes.POINTER(ka_msg)]),
+    "ka_debug_device_cache": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                               ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32)]),
     "ka_debug_pred_keep": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32,
                                             ctypes.POINTER(ctypes.c_int32)]),
     "ka_debug_fail_stage": (ctypes.c_int32, [c_vp, ctypes.c_int32]),
     "ka_debug_kill_dispatcher": (ctypes.c_int32, [c_vp]),
     "ka_system_monitor": (ctypes.c_int32, [c_vp, MONITOR_FN, c_vp]),
-    "ka_actor_enable_graph": (ctypes.c_int32, [c_vp, ctypes.c_int32]),
     "ka_bench_request_loop": (ctypes.c_int32, [c_vp, ctypes.POINTER(ka_msg), ctypes.c_uint32, ctypes.c_uint32,
                                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
     "ka_bench_direct_chain": (ctypes.c_int32, [ctypes.POINTER(ka_stage_desc), ctypes.c_uint32, c_vp, ctypes.c_uint64,
@@ -294,6 +299,13 @@ def ka_compact_static(d_in, n: int, d_n, pred: int, param: int, xform: int, d_ou
                                  _tile(tile), stream_ptr(stream))
 
 
+def ka_compact_static_workspace(stream=None):
+    """(status, device address, bytes) of the current device's shared array."""
+    p, nb = c_vp(0), ctypes.c_uint64(0)
+    s = lib.ka_compact_static_workspace(stream_ptr(stream), ctypes.byref(p), ctypes.byref(nb))
+    return s, (p.value or 0), nb.value
+
+
 def ka_three_phase_workspace_size(capacity: int):
     out = ctypes.c_uint64(0)
     s = lib.ka_three_phase_workspace_size(capacity, ctypes.byref(out))
@@ -367,6 +379,16 @@ def ka_tile_for(kernel: int, n: int):
     t = ka_tile(0, 0)
     s = lib.ka_tile_for(kernel, n, ctypes.byref(t))
     return s, (t.block, t.ipt)
+
+
+def ka_debug_device_cache(devices, values):
+    """(status, [value each lookup returned]) for the per-device cache hook."""
+    n = len(devices)
+    d = (ctypes.c_int32 * n)(*devices)
+    v = (ctypes.c_int32 * n)(*values)
+    o = (ctypes.c_int32 * n)()
+    s = lib.ka_debug_device_cache(d, v, n, o)
+    return s, list(o)
 
 
 def ka_debug_pred_keep(pred: int, param: int, x: int):
@@ -503,10 +525,6 @@ def ka_system_monitor(sys_h, fn, user=None) -> int:
     """fn(user, reason) is called once when the dispatcher dies; keep `fn` (a
     MONITOR_FN) alive while the system exists."""
     return lib.ka_system_monitor(sys_h, fn, user)
-
-
-def ka_actor_enable_graph(actor_h, enable: int = 1) -> int:
-    return lib.ka_actor_enable_graph(actor_h, enable)
 
 
 def ka_serve_run(sys_h, reqs, n_reqs: int, opt, results, stats) -> int:

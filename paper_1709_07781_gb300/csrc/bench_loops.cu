@@ -124,6 +124,11 @@ ka_status ka_bench_direct_chain(const ka_stage_desc *stages, uint32_t n_stages, 
             o = cur;
             o.push_back(y);
             break;
+        case KA_STAGE_PREPARE:  // first stage only: d_in = k chunk ids, then k literals
+            if (i != 0 || cur.size() != 1) s = KA_E_TYPE;
+            if (s == KA_OK) s = alloc(2 * cur[0].cap, &y);
+            o.push_back(y);
+            break;
         case KA_STAGE_EMPTY: o = cur; break;
         case KA_STAGE_MANDELBROT:
             if (d.pred <= 0 || d.xform == 0) s = KA_E_ARG;
@@ -178,6 +183,9 @@ ka_status ka_bench_direct_chain(const ka_stage_desc *stages, uint32_t n_stages, 
             }
             case KA_STAGE_SCATTER:
                 e = launch_scatter(c[0].ptr, c[1].ptr, c[2].ptr, nn, np, o[0].ptr, o[0].count, st);
+                break;
+            case KA_STAGE_PREPARE:
+                e = launch_prepare_index(c[0].ptr, c[0].ptr + c[0].cap, nn, np, o[0].ptr, o[0].count, st);
                 break;
             case KA_STAGE_EMPTY: e = launch_empty(st); break;
             case KA_STAGE_MANDELBROT:  // the rectangle of the paper's workload (Sec. 5.4)

@@ -158,6 +158,13 @@ ka_status ka_debug_pred_keep(int32_t pred, uint32_t param, uint32_t x, int32_t *
     return KA_OK;
 }
 
+ka_status ka_debug_device_cache(const int32_t *devices, const int32_t *values, uint32_t n, int32_t *out) {
+    if (n && (!devices || !values || !out)) return KA_E_ARG;
+    PerDeviceInt cache{};
+    for (uint32_t i = 0; i < n; ++i) out[i] = per_device_value(cache, devices[i], [&] { return values[i]; });
+    return KA_OK;
+}
+
 ka_status ka_workspace_set_spin_limit(void *d_ws, uint32_t polls, void *stream) {
     if (!d_ws || polls == 0) return KA_E_ARG;
     k_ws_set_spin<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<WsHeader *>(d_ws), polls);

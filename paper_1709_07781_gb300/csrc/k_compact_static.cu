@@ -96,3 +96,15 @@ extern "C" ka_status ka_compact_static(const uint32_t *d_in, uint64_t n, const u
     L.tile = resolve_tile(KA_KERNEL_COMPACT, n, tile);
     return launch_compact(L, st);
 }
+
+// The array as a workspace, so that the workspace calls (status, clear, spin
+// limit) work on it: a device error of a call is recorded in its header.
+extern "C" ka_status ka_compact_static_workspace(void *stream, void **d_ws, uint64_t *bytes) {
+    if (!d_ws || !bytes) return KA_E_ARG;
+    void *ws = nullptr;
+    const ka_status s = static_scratch(static_cast<cudaStream_t>(stream), &ws);
+    if (s != KA_OK) return s;
+    *d_ws = ws;
+    *bytes = kStaticScratchBytes;
+    return KA_OK;
+}

@@ -1217,10 +1217,6 @@ ka_status ka_debug_fail_stage(ka_actor *h, int32_t fail_after) {
     return KA_OK;
 }
 
-ka_status ka_actor_enable_graph(ka_actor *h, int32_t) {
-    return actor_of(h) ? KA_E_UNSUPPORTED : KA_E_STALE;
-}
-
 // --- messages ----------------------------------------------------------------
 ka_status ka_request(ka_actor *h, const ka_msg *in, ka_request_h **out) {
     Actor *c = actor_of(h);

@@ -130,6 +130,15 @@ struct Run {
     void *ws_plain = nullptr;
     uint64_t ws_plain_bytes = 0;
 
+    // value-mode read-backs in flight on `readback` (oldest first), each with
+    // the event recorded after its copy; and events free for reuse
+    struct Readback {
+        uint32_t req;
+        cudaEvent_t ev;
+    };
+    std::deque<Readback> rb_pending;
+    std::vector<cudaEvent_t> rb_free;
+
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
     double arrival(uint32_t r) const { return reqs[r].arrival_s * scale; }
 };
@@ -144,8 +153,33 @@ ka_status check_request(const ka_serve_request &q) {
     return KA_OK;
 }
 
-// Marks request r done with status s; copies its data out in value mode and
-// returns its buffer to the pool.
+// Request r is complete: its result (and in value mode its data) is on the host.
+void mark_done(Run &R, uint32_t r) {
+    ka_serve_result &o = R.res[r];
+    o.done_s = R.now();
+    R.last_done = o.done_s;
+    if (o.status == KA_OK) R.st.elements += R.reqs[r].n;
+    R.finished += 1;
+}
+
+// Read-backs whose copies have landed complete their requests, in order.
+ka_status poll_readbacks(Run &R) {
+    while (!R.rb_pending.empty()) {
+        const Run::Readback rb = R.rb_pending.front();
+        const cudaError_t e = cudaEventQuery(rb.ev);
+        if (e == cudaErrorNotReady) break;
+        R.rb_pending.pop_front();
+        R.rb_free.push_back(rb.ev);
+        if (e != cudaSuccess) R.res[rb.req].status = cuda_status(e);
+        mark_done(R, rb.req);
+    }
+    return KA_OK;
+}
+
+// Marks request r finished with status s and returns its buffer to the pool.
+// In value mode the data is copied out on the read-back stream first: the
+// buffer is freed on that stream after the copy, and the request completes
+// when poll_readbacks sees the copy done, so the loop never waits for it.
 void finish(Run &R, uint32_t r, uint32_t count, ka_status s) {
     ka_serve_result &o = R.res[r];
     const ka_serve_request &q = R.reqs[r];
@@ -154,21 +188,36 @@ void finish(Run &R, uint32_t r, uint32_t count, ka_status s) {
     if (s == KA_OK && q.h_out && R.buf[r]) {
         const uint64_t m = std::min<uint64_t>(count, q.h_out_cap);
         if (m) {
-            cudaError_t e = cudaMemcpyAsync(q.h_out, R.buf[r], m * 4, cudaMemcpyDeviceToHost, R.readback);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(R.readback);
-            if (e != cudaSuccess) o.status = cuda_status(e);
+            cudaEvent_t ev = nullptr;
+            if (!R.rb_free.empty()) {
+                ev = R.rb_free.back();
+                R.rb_free.pop_back();
+            }
+            cudaError_t e = ev ? cudaSuccess : cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(q.h_out, R.buf[r], m * 4, cudaMemcpyDeviceToHost, R.readback);
+            if (e == cudaSuccess) e = cudaEventRecord(ev, R.readback);
+            if (e == cudaSuccess) {
+                cudaFreeAsync(R.buf[r], R.readback);  // after the copy, in the read-back stream's order
+                R.buf[r] = nullptr;
+                R.in_use -= bytes_for(q.n);
+                R.inflight -= 1;
+                R.rb_pending.push_back({r, ev});
+                return;
+            }
+            if (ev) R.rb_free.push_back(ev);
+            o.status = cuda_status(e);
+            cudaStreamSynchronize(R.readback);  // the buffer may still be read: wait before freeing it
         }
     }
     if (R.buf[r]) {
+        const double t_free = R.now();
         cudaFreeAsync(R.buf[r], R.stream);
+        R.st.max_free_s = std::max(R.st.max_free_s, R.now() - t_free);
         R.buf[r] = nullptr;
         R.in_use -= bytes_for(q.n);
         R.inflight -= 1;
     }
-    o.done_s = R.now();
-    R.last_done = o.done_s;
-    if (o.status == KA_OK) R.st.elements += q.n;
-    R.finished += 1;
+    mark_done(R, r);
 }
 
 // Admits the request at the head of the queue if the budget and the in-flight
@@ -179,7 +228,10 @@ bool admit_head(Run &R, uint32_t *out) {
     const uint64_t b = bytes_for(R.reqs[r].n);
     if (R.in_use + b > R.budget) return false;
     void *p = nullptr;
-    if (cudaMallocFromPoolAsync(&p, b, R.pool, R.stream) != cudaSuccess) {
+    const double t_alloc = R.now();
+    const cudaError_t ea = cudaMallocFromPoolAsync(&p, b, R.pool, R.stream);
+    R.st.max_alloc_s = std::max(R.st.max_alloc_s, R.now() - t_alloc);
+    if (ea != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -524,6 +576,9 @@ ka_status setup(Run &R, uint32_t max_n) {
 
 void teardown(Run &R) {
     if (R.stream) cudaStreamSynchronize(R.stream);
+    if (R.readback) cudaStreamSynchronize(R.readback);
+    for (const Run::Readback &rb : R.rb_pending) cudaEventDestroy(rb.ev);
+    for (cudaEvent_t e : R.rb_free) cudaEventDestroy(e);
     for (void *&p : R.buf)
         if (p) {
             cudaFreeAsync(p, R.stream);
@@ -591,8 +646,15 @@ extern "C" ka_status ka_serve_run(ka_system *sys, const ka_serve_request *reqs, 
     s = setup(R, max_n);
     if (s == KA_OK) {
         R.t0 = Clock::now();
+        double step_t0 = 0.0;
         while (R.finished < R.n) {
             const double t = R.now();
+            if (step_t0 > 0.0) {
+                const double step = t - step_t0;
+                R.st.max_step_s = std::max(R.st.max_step_s, step);
+                if (step > 1e-3) R.st.slow_steps += 1;
+            }
+            step_t0 = t;
             while (R.next < R.n && R.arrival(R.order[R.next]) <= t) {
                 const uint32_t r = R.order[R.next++];
                 const ka_status v = check_request(reqs[r]);
@@ -605,15 +667,24 @@ extern "C" ka_status ka_serve_run(ka_system *sys, const ka_serve_request *reqs, 
                 R.waiting.push_back(r);
             }
             bool done_some = false, issued = false;
+            const double t_poll = R.now();
             s = R.mode != 1 ? poll_ticks(R, &done_some) : poll_plain(R, &done_some);
+            if (s == KA_OK) s = poll_readbacks(R);
+            const double t_issue = R.now();
+            R.st.max_poll_s = std::max(R.st.max_poll_s, t_issue - t_poll);
             if (s == KA_OK) s = R.mode != 1 ? issue_tick(R, &issued) : issue_plain(R, &issued);
+            R.st.max_issue_s = std::max(R.st.max_issue_s, R.now() - t_issue);
             if (s != KA_OK) break;
-            const bool busy = R.mode != 1 ? R.tick_used > 0 : !R.plain_inflight.empty();
+            const bool busy = (R.mode != 1 ? R.tick_used > 0 : !R.plain_inflight.empty()) || !R.rb_pending.empty();
             if (!done_some && !issued) {
                 if (!busy && R.waiting.empty() && R.next < R.n) {
-                    // idle until the next arrival (sleep coarsely, then spin)
+                    // Idle until the next arrival: short sleeps while it is more
+                    // than half a millisecond away (a sleep may overrun by tens of
+                    // microseconds, and a long one by much more when the thread
+                    // is descheduled), then spin.
                     const double wait = R.arrival(R.order[R.next]) - R.now();
-                    if (wait > 2e-4) std::this_thread::sleep_for(std::chrono::duration<double>(wait - 1e-4));
+                    if (wait > 5e-4) std::this_thread::sleep_for(std::chrono::microseconds(200));
+                    step_t0 = 0.0;  // an idle wait is not a stall
                 } else if (!busy && !R.waiting.empty()) {
                     // the head request cannot be admitted and nothing will free memory
                     const uint32_t r = R.waiting.front();

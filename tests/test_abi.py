@@ -179,3 +179,15 @@ def test_last_cuda_error_names_the_failure(ka):
     s, _ = ka.ka_system_create(0)
     assert s == ka.KA_E_CUDA
     assert ka.ka_last_cuda_error() != 0
+
+
+def test_launch_caches_are_keyed_by_device(ka):
+    """The occupancy and resident-grid caches hold one value per device
+    ordinal: a second device computes its own, a failed computation (a value
+    <= 0) is not kept, and an ordinal outside the table is never cached."""
+    s, out = ka.ka_debug_device_cache([0, 1, 0, 1, 2, 0], [10, 20, 99, 99, 30, 99])
+    assert s == 0 and out == [10, 20, 10, 20, 30, 10]
+    s, out = ka.ka_debug_device_cache([3, 3, 3], [-1, 7, 9])
+    assert s == 0 and out == [-1, 7, 7]
+    s, out = ka.ka_debug_device_cache([70, 70, -1, -1], [5, 6, 4, 8])
+    assert s == 0 and out == [5, 6, 4, 8]
