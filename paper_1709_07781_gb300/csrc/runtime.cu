@@ -201,8 +201,22 @@ struct Actor {
     std::atomic<uint64_t> processed{0};
 };
 
+struct Request;
+
+// The message of a request: its references as it travels from stage to stage
+// (one message per request, kept inside the request object).
+struct Msg : QNode {
+    Request *req = nullptr;
+    int stage = 0;
+    int n_refs = 0;
+    Ref *refs[KA_MSG_MAX_REFS] = {nullptr, nullptr, nullptr, nullptr};
+    uint64_t seed = 0;
+    uint64_t gen_n = 0;
+};
+
 struct Request {
     uint64_t handle = 0;
+    Msg msg;  // travels through the stages while the request is in flight
     System *sys = nullptr;
     std::vector<Actor *> stages;  // retained
     // value mode
@@ -225,18 +239,15 @@ struct Request {
     // stage has been issued; the last holder frees the request
     std::atomic<int> holders{1};
     std::atomic<bool> recorded{false};  // event recorded after the last stage
-    std::atomic<bool> claimed{false};   // a thread has taken on fulfilling the promise
-    std::atomic<bool> waiting{false};   // a receiver is polling for completion
+    std::atomic<bool> blocked{false};   // a receiver is (about to be) blocked on cv
+    // The two flags the completion thread watches while a receiver polls, on
+    // a cache line of their own: the fulfilling receiver's writes to the
+    // result fields above then do not contend with the watcher's reads.
+    alignas(64) std::atomic<bool> claimed{false};  // a thread has taken on fulfilling the promise
+    std::atomic<bool> waiting{false};              // a receiver is polling for completion
+    char pad_[62];
 };
 
-struct Msg : QNode {
-    Request *req = nullptr;
-    int stage = 0;
-    int n_refs = 0;
-    Ref *refs[KA_MSG_MAX_REFS] = {nullptr, nullptr, nullptr, nullptr};
-    uint64_t seed = 0;
-    uint64_t gen_n = 0;
-};
 
 struct Completion {
     Request *req;
@@ -454,12 +465,15 @@ static void post(Actor *a, Msg *m) {
 
 static void complete(Request *r, ka_status st) {
     System *s = r->sys;
-    {
-        std::lock_guard<std::mutex> l(r->mu);
-        r->status = st;
-        r->done.store(true, std::memory_order_release);
+    r->status = st;
+    r->done.store(true, std::memory_order_seq_cst);
+    // A receiver that polls sees `done`; one that blocks on cv has set
+    // `blocked` first (both sequentially consistent, so at least one side sees
+    // the other), and is woken under the lock.
+    if (r->blocked.load(std::memory_order_seq_cst)) {
+        { std::lock_guard<std::mutex> l(r->mu); }
+        r->cv.notify_all();
     }
-    r->cv.notify_all();
     s->inflight.fetch_sub(1);
 }
 
@@ -470,9 +484,7 @@ static void release_msg_refs(Msg *m) {
 
 static void fail_request(Msg *m, ka_status st) {
     release_msg_refs(m);
-    Request *r = m->req;
-    delete m;
-    complete(r, st);
+    complete(m->req, st);
 }
 
 // Runs one stage for message m; on success fills outs/n_outs.
@@ -650,7 +662,6 @@ static Actor *process(System *s, Actor *a, Msg *m) {
     }
     // Last stage: read the result length back and fulfil the promise once the
     // stream reaches this point.
-    delete m;
     r->result.assign(outs, outs + n_outs);
     // The length (and in debug mode the device error word) is stored into the
     // request's host-mapped slot by a one-thread kernel on the stream.
@@ -807,8 +818,10 @@ static void completer_main(System *s) {
         Request *r = c.req;
         // A receiver polling r fulfils it itself; this thread stays out of the
         // driver meanwhile and steps in only once no receiver is polling.
+        // (checked every 20 us: a polling receiver claims its request within
+        // microseconds, and a tighter watch only costs it coherence misses)
         while (!r->claimed.load(std::memory_order_acquire) && r->waiting.load(std::memory_order_acquire))
-            std::this_thread::yield();
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
         if (!r->claimed.load(std::memory_order_acquire)) {
             const ka_status st = cuda_status(cudaEventSynchronize(r->event));
             if (!r->claimed.exchange(true, std::memory_order_acq_rel)) finalize(s, r, st);
@@ -871,6 +884,7 @@ static void request_recycle(Request *r) {
     r->recorded.store(false, std::memory_order_relaxed);
     r->claimed.store(false, std::memory_order_relaxed);
     r->waiting.store(false, std::memory_order_relaxed);
+    r->blocked.store(false, std::memory_order_relaxed);
     System *s = r->sys;
     std::lock_guard<std::mutex> l(s->req_mu);
     s->req_free.push_back(r);
@@ -1225,28 +1239,25 @@ ka_status ka_request(ka_actor *h, const ka_msg *in, ka_request_h **out) {
     System *s = c->sys;
     if (s->stop.load() || s->dead.load()) return KA_E_CLOSED;
     if (in->n_refs > KA_MSG_MAX_REFS) return KA_E_ARG;
-    Msg *m = new Msg;
+    Request *r = request_new(s);
+    if (!r) return KA_E_OOM;
+    Msg *m = &r->msg;
+    m->n_refs = 0;
     m->seed = in->seed;
     m->gen_n = in->gen_n;
     // resolve references (the request holds its own)
     {
         std::lock_guard<std::mutex> l(g_refs.mutex());
         for (uint32_t i = 0; i < in->n_refs; ++i) {
-            Ref *r = g_refs.get_locked(reinterpret_cast<uint64_t>(in->refs[i]));
-            if (!r) {
-                for (int j = 0; j < m->n_refs; ++j) ref_drop(m->refs[j]);
-                delete m;
+            Ref *x = g_refs.get_locked(reinterpret_cast<uint64_t>(in->refs[i]));
+            if (!x) {
+                release_msg_refs(m);
+                request_recycle(r);
                 return KA_E_STALE;
             }
-            ref_retain(r);
-            m->refs[m->n_refs++] = r;
+            ref_retain(x);
+            m->refs[m->n_refs++] = x;
         }
-    }
-    Request *r = request_new(s);
-    if (!r) {
-        release_msg_refs(m);
-        delete m;
-        return KA_E_OOM;
     }
     r->h_out = in->h_out;
     r->h_out_cap = in->h_out_cap;
@@ -1270,7 +1281,7 @@ ka_status ka_request(ka_actor *h, const ka_msg *in, ka_request_h **out) {
             if (u) ref_drop(u);
             m->refs[0] = nullptr;
             for (int j = 1; j < m->n_refs; ++j) ref_drop(m->refs[j]);
-            delete m;
+            m->n_refs = 0;
             request_recycle(r);
             return st;
         }
@@ -1282,16 +1293,19 @@ ka_status ka_request(ka_actor *h, const ka_msg *in, ka_request_h **out) {
     }
     m->req = r;
     m->stage = 0;
-    r->handle = g_requests.add(r);
     s->inflight.fetch_add(1);
-    *out = reinterpret_cast<ka_request_h *>(r->handle);
     // Inline dispatch: while no thread runs actors and the next actor has no
     // mail queued, run the stages here; the rest goes through the mailboxes.
+    // The handle is registered after the first launches: only the caller
+    // uses it, and the request stays alive on the caller's hold until it
+    // receives.
     Actor *a = r->stages[0];
     if (!s->kill_requested.load() && s->dispatch_mu.try_lock()) {
         while (a && actor_idle(a)) a = process(s, a, m);
         s->dispatch_mu.unlock();
     }
+    r->handle = g_requests.add(r);
+    *out = reinterpret_cast<ka_request_h *>(r->handle);
     if (a) post(a, m);
     return KA_OK;
 }
@@ -1326,6 +1340,7 @@ ka_status ka_receive(ka_request_h *h, int64_t timeout_ns, ka_msg *out) {
         }
         r->waiting.store(false, std::memory_order_release);
         if (!r->done.load(std::memory_order_acquire)) {
+            r->blocked.store(true, std::memory_order_seq_cst);
             std::unique_lock<std::mutex> l(r->mu);
             if (timeout_ns < 0) {
                 r->cv.wait(l, [&] { return r->done.load(); });
