@@ -14,6 +14,8 @@ import oracle  # noqa: E402
 from gpu_util import SENTINEL, Workspace, empty, stream, to_dev, to_host, word  # noqa: E402
 
 TMA_SHAPES = [(768, 16), (512, 16), (256, 16)]
+# entries per tile of each shape's compaction (25 compute warps for (768, 16))
+TILE = {(768, 16): 12800, (512, 16): 8192, (256, 16): 4096}
 
 
 @pytest.fixture(scope="module")
@@ -37,6 +39,7 @@ def compact(ka, d_x, n, pred, param, shape, xform=0, d_n=None, out=None, cap=Non
 
 @pytest.mark.parametrize("shape", TMA_SHAPES)
 @pytest.mark.parametrize("n", [1, 4095, 4096, 8191, 8192, 8193, 3 * 8192 + 5, 12287, 12288, 12289, 3 * 12288 + 5,
+                               12799, 12800, 12801, 3 * 12800 + 5,
                                1 << 20, (1 << 22) + 12345, (1 << 23) + 1])
 def test_tma_sizes(ka, shape, n):
     x = ki.uniform_u32(n + 7, n)
@@ -101,7 +104,7 @@ def test_tma_unaligned_output(ka, shape, out_off):
 def test_tma_unaligned_input(ka, shape, in_off):
     """Input views starting 4, 8 or 12 bytes past a 16-byte boundary: the tiles
     are shifted back to the boundary and the lead entries belong to no tile."""
-    T = shape[0] * shape[1]
+    T = TILE[shape]
     for n in [1, 2, 3, 5, T - in_off, T - in_off + 1, T, 3 * T + 7, (1 << 21) + 3]:
         x = ki.uniform_u32(70 + in_off, n + in_off)
         buf = to_dev(x, pad=16)
@@ -143,7 +146,7 @@ def test_tma_low_selectivity(ka, shape, s):
     """Selectivities whose segments keep at most 32 entries (compacted into
     the warps' spill rings and written out by the look-back warp), around 32
     (both kinds in one tile) and just above it."""
-    T = shape[0] * shape[1]
+    T = TILE[shape]
     for n in [5, T - 1, 3 * T + 5, (1 << 22) + 12345]:
         x = ki.uniform_u32(int(s * 1e4) + n, n)
         out, k = compact(ka, to_dev(x), n, "lt", ki.threshold_for(s), shape)
