@@ -127,12 +127,31 @@ __global__ void __launch_bounds__(kEwBlock) k_prepare_index(const uint32_t *a, c
     const uint32_t stride = gridDim.x * blockDim.x;
     if (tid == 0 && n_out) *n_out = 2u * k;
     if (vec) {
+        // eight independent 16-byte loads per array in flight per thread (a
+        // single pair per iteration leaves too few bytes in flight per SM to
+        // cover the memory latency), consecutive threads on consecutive
+        // chunks; the index is written with streaming stores (written once,
+        // read by the next stage from DRAM or whatever of it L2 still holds)
+        constexpr uint32_t U = 8;
         const uint32_t k4 = k / 4;
-        for (uint32_t i = tid; i < k4; i += stride) {
-            const uint4 p = ld_stream_v4(a + uint64_t(i) * 4);
-            const uint4 q = ld_stream_v4(b + uint64_t(i) * 4);
-            st_v4(index + uint64_t(i) * 8, make_uint4(p.x, q.x, p.y, q.y));
-            st_v4(index + uint64_t(i) * 8 + 4, make_uint4(p.z, q.z, p.w, q.w));
+        for (uint32_t i0 = tid; i0 < k4; i0 += U * stride) {
+            uint4 p[U], q[U];
+#pragma unroll
+            for (uint32_t u = 0; u < U; ++u) {
+                const uint64_t i = uint64_t(i0) + uint64_t(u) * stride;
+                if (i < k4) {
+                    p[u] = ld_stream_v4(a + i * 4);
+                    q[u] = ld_stream_v4(b + i * 4);
+                }
+            }
+#pragma unroll
+            for (uint32_t u = 0; u < U; ++u) {
+                const uint64_t i = uint64_t(i0) + uint64_t(u) * stride;
+                if (i < k4) {
+                    __stcs(reinterpret_cast<uint4 *>(index + i * 8), make_uint4(p[u].x, q[u].x, p[u].y, q[u].y));
+                    __stcs(reinterpret_cast<uint4 *>(index + i * 8 + 4), make_uint4(p[u].z, q[u].z, p[u].w, q[u].w));
+                }
+            }
         }
         for (uint32_t e = k4 * 4 + tid; e < k; e += stride) {
             index[2ull * e] = a[e];
