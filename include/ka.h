@@ -102,8 +102,8 @@ typedef enum ka_pred_kind {
  * select the warp-specialised TMA kernels (compaction, scan, batch): compute
  * warps of 512 entries each, plus a look-back warp and a producer warp; block
  * / 32 compute warps, except that the compaction and the scan of (768, 16)
- * have 25 (tiles of 12800 entries; its batch kernel has 24). A tile holds 512
- * to 12800 entries.
+ * have 26 (tiles of 13312 entries; its batch kernel has 24). A tile holds 512
+ * to 13312 entries.
  * A NULL tile, or {0, 0}, picks the library default (or the autotuned shape
  * once ka_autotune has run for that kernel). */
 typedef struct ka_tile {

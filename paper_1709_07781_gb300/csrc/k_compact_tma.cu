@@ -10,8 +10,8 @@ using namespace tma;
 
 namespace {
 
-// tile (768, 16): 25 compute warps, 12800 entries, 4 stages of 50 KiB and a 25 KiB
-//                 spill ring (all but 128 bytes of the 227 KiB a block may have), 1 block per SM;
+// tile (768, 16): 26 compute warps, 13312 entries, 4 stages of 52 KiB and a 13 KiB
+//                 spill ring (8 slots of 16 entries per warp), 1 block per SM;
 // tile (512, 16): 16 compute warps, 8192 entries, 3 stages of 32 KiB, 2 blocks per SM;
 // tile (256, 16): 8 compute warps, 4096 entries, 4 stages of 16 KiB, 3 blocks per SM.
 ka_status launch_tma(const TmaArgs &a, ka_tile tile, bool scan, int32_t pk, uint64_t cap, cudaStream_t stream) {

@@ -14,8 +14,8 @@ import oracle  # noqa: E402
 from gpu_util import SENTINEL, Workspace, empty, stream, to_dev, to_host, word  # noqa: E402
 
 TMA_SHAPES = [(768, 16), (512, 16), (256, 16)]
-# entries per tile of each shape's compaction (25 compute warps for (768, 16))
-TILE = {(768, 16): 12800, (512, 16): 8192, (256, 16): 4096}
+# entries per tile of each shape's compaction (26 compute warps for (768, 16))
+TILE = {(768, 16): 13312, (512, 16): 8192, (256, 16): 4096}
 
 
 @pytest.fixture(scope="module")
@@ -39,7 +39,7 @@ def compact(ka, d_x, n, pred, param, shape, xform=0, d_n=None, out=None, cap=Non
 
 @pytest.mark.parametrize("shape", TMA_SHAPES)
 @pytest.mark.parametrize("n", [1, 4095, 4096, 8191, 8192, 8193, 3 * 8192 + 5, 12287, 12288, 12289, 3 * 12288 + 5,
-                               12799, 12800, 12801, 3 * 12800 + 5,
+                               13311, 13312, 13313, 3 * 13312 + 5,
                                1 << 20, (1 << 22) + 12345, (1 << 23) + 1])
 def test_tma_sizes(ka, shape, n):
     x = ki.uniform_u32(n + 7, n)
@@ -129,23 +129,23 @@ def test_tma_unaligned_input(ka, shape, in_off):
 
 def varied_segments(seed, n, seg=512):
     """Uniform entries rewritten so that `x < 2^31` keeps them with a
-    selectivity that changes every `seg` entries (0, 2, 6.25, 8, 50 or 100 %):
+    selectivity that changes every `seg` entries (0, 1, 3, 4.5, 50 or 100 %):
     the kept counts of one tile's 512-entry segments then fall on both sides
-    of the 32 entries a segment may keep and still be spilled, and each tile
+    of the 16 entries a segment may keep and still be spilled, and each tile
     mixes spilled and held segments."""
     u = ki.uniform_u32(seed, n)
     rng = np.random.default_rng(seed)
-    frac = np.array([0.0, 0.02, 0.0625, 0.08, 0.5, 1.0])[rng.integers(0, 6, size=(n + seg - 1) // seg)]
+    frac = np.array([0.0, 0.01, 0.03, 0.045, 0.5, 1.0])[rng.integers(0, 6, size=(n + seg - 1) // seg)]
     keep = (u.astype(np.float64) / 2.0**32) < np.repeat(frac, seg)[:n]
     return np.where(keep, u >> np.uint32(1), u | np.uint32(0x80000000)).astype(np.uint32)
 
 
 @pytest.mark.parametrize("shape", TMA_SHAPES)
-@pytest.mark.parametrize("s", [0.001, 0.01, 0.03, 0.0625, 0.08])
+@pytest.mark.parametrize("s", [0.001, 0.01, 0.02, 0.03, 0.04, 0.0625])
 def test_tma_low_selectivity(ka, shape, s):
-    """Selectivities whose segments keep at most 32 entries (compacted into
-    the warps' spill rings and written out by the look-back warp), around 32
-    (both kinds in one tile) and just above it."""
+    """Selectivities whose segments keep at most 16 entries (compacted into
+    the warps' spill rings and written out by their warps 7 tiles later),
+    around 16 (both kinds in one tile) and above it."""
     T = TILE[shape]
     for n in [5, T - 1, 3 * T + 5, (1 << 22) + 12345]:
         x = ki.uniform_u32(int(s * 1e4) + n, n)

@@ -17,7 +17,7 @@ from gpu_util import SENTINEL, Workspace, empty, stream, to_dev, to_host, word  
 
 SHAPES = [(128, 4), (128, 8), (128, 16), (256, 4), (256, 8), (256, 16), (512, 4), (512, 8)]
 SIZES = [0, 1, 3, 4, 5, 127, 511, 512, 513, 1023, 1025, 2047, 2048, 2049, 4095, 4096, 4097, 3 * 4096 + 17,
-         12287, 12288, 12289, 12799, 12800, 12801, 65537, (1 << 20) + 3]
+         12287, 12288, 12289, 13311, 13312, 13313, 65537, (1 << 20) + 3]
 TMA_SHAPES = [(768, 16), (512, 16)]  # (256, 16) is in SHAPES
 PREDS = [("and_mask_eq0", 3), ("lt", ki.threshold_for(0.5)), ("topbits_lt", 8), ("popc_odd", 0),
          ("mod_ne0", 3), ("ne", 0), ("mod_ne0", 12), ("topbits_lt", 0), ("lt", 0), ("lt", 0xFFFFFFFF)]

@@ -122,7 +122,7 @@ def test_predicate_and_hash_max_length(ka):
 
 @pytest.mark.parametrize("lead", [0, 1])
 def test_compact_tma_max_length(ka, lead):
-    """Tile (768, 16): 12800 entries per tile, which does not divide 2^32, so
+    """Tile (768, 16): 13312 entries per tile, which does not divide 2^32, so
     the last tile's later segments lie past 2^32. Input x_j = j + lead (the
     view starts `lead` entries past a 16-byte boundary); keep x & 3 == 0:
     the multiples of 4 in [lead, lead + n)."""
