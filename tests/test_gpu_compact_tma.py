@@ -156,6 +156,20 @@ def test_tma_low_selectivity(ka, shape, s):
 
 
 @pytest.mark.parametrize("shape", TMA_SHAPES)
+@pytest.mark.parametrize("s", [0.005, 0.03, 0.3])
+def test_tma_hash_transform_spilled_and_held(ka, shape, s):
+    """The hash transform on both write-out paths: the spilled and the held
+    segments must both store the hashed values that passed the test."""
+    n = (1 << 22) + 1001
+    x = ki.uniform_u32(900 + int(1000 * s), n)
+    t = ki.threshold_for(s)
+    out, k = compact(ka, to_dev(x), n, "lt", t, shape, xform=1)
+    y, ek = oracle.compact(oracle.map_hash(x), "lt", t)
+    assert k == ek and np.array_equal(to_host(out, k), y)
+    assert np.all(to_host(out)[k:n + 16] == SENTINEL)
+
+
+@pytest.mark.parametrize("shape", TMA_SHAPES)
 @pytest.mark.parametrize("in_off", [0, 1, 2, 3])
 def test_tma_mixed_segments(ka, shape, in_off):
     """Tiles whose segments keep anywhere from none to all of their entries,
