@@ -292,11 +292,16 @@ ka_status ka_batch_workspace_size(uint32_t max_items, uint64_t total_capacity, c
  * item i's kept entries go to out_i[0..k_i) in order and *count_i = k_i.
  * max_items must be the value the workspace was sized for (it fixes the
  * layout); n_items <= max_items. `grid` = 0 picks one persistent block per SM
- * slot. Two launches: a plan kernel (live lengths, canonical predicates and
- * per-item tile offsets) and one persistent kernel that walks the flattened
- * (item, tile) ticket space with a decoupled look-back per item. Because the
- * plan records each live length before any compaction runs, count_i may
- * alias n_ptr_i (the paper's in_out configuration word). An invalid item
+ * slot. Two launches: a plan kernel (one block per 256 items: live lengths,
+ * canonical predicates, and per-item tile offsets by a scan chained across
+ * its blocks through one status word per block; for the TMA shapes also the
+ * item of each tile of an item of at most 8 tiles) and one persistent kernel
+ * that walks the flattened (item, tile) ticket space with a decoupled
+ * look-back per item. A workspace with fewer status words than
+ * ceil(n_items / 256) returns KA_E_WORKSPACE (ka_batch_workspace_size always
+ * leaves max_items + 1 or more). Because the plan records each live length
+ * before any compaction runs, count_i may alias n_ptr_i (the paper's in_out
+ * configuration word). An invalid item
  * (unknown predicate, zero modulus) gets count 0 and sets the workspace error
  * KA_E_ARG; more tiles than the workspace holds set KA_E_WORKSPACE. */
 ka_status ka_compact_batch(const ka_batch_item *d_items, uint32_t n_items, uint32_t max_items, void *d_ws,

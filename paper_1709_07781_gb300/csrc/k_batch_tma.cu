@@ -6,8 +6,10 @@
 // back to a 16-byte boundary as in the single-array kernel). Block b of the G
 // resident blocks takes flattened tiles b, b + G, b + 2G, ... The roles are
 // those of the single-array kernel:
-//   * the producer warp finds the item of each of its tiles (a warp-wide
-//     search starting at the previous tile's item), records the item's
+//   * the producer warp finds the item of each of its tiles (the plan's map
+//     word for a tile of a small item, else a warp-wide search starting at
+//     the item of its previous tile; both two tiles ahead, so that no load
+//     waits between two copies), records the item's
 //     output, count word, predicate and the tile's valid range in the
 //     stage's slot, and copies the tile with cp.async.bulk; a partial last
 //     tile is copied rounded up to 16 bytes (the extra entries lie in the
@@ -85,28 +87,70 @@ __global__ void __launch_bounds__((CWW + 2) * 32, MINB) k_batch_tma(const BatchA
 
     if (warp == CWW + 1) {
         // ------------------------------------------------------------------ producer warp
-        // The item of each flattened tile was written beside the tile's status
-        // word (k_batch_tile_items). Tile j + 2's item index and tile j + 1's
-        // item and plan records are loaded while tile j is issued, so no
-        // dependent load sits between two copies. A tile's records are spread
-        // over the warp, one word per lane: lanes 0-11 the item (48 bytes),
-        // 12-19 the plan (32 bytes), 20 the item's first tile.
+        // Tiles b, b + G, ... lie in non-decreasing items. The item of tile
+        // jj + 2 is found while tile jj is issued: its map word (read three
+        // tiles ahead, which also brings the tile's status sector into L2
+        // before its aggregate is stored and polled), written by the plan for
+        // tiles of small items, or else ballots over the window
+        // tile_off[i + 1 .. i + 128] after the item i of tile jj + 1, loaded
+        // one tile earlier (a 32-ary search from there when the window ends
+        // first; G tiles of items that are not small span fewer items).
+        // Tile jj + 1's item and plan records are loaded then as well, one
+        // word per lane: lanes 0-11 the item (48 bytes), 12-19 the plan (32
+        // bytes), 20 the item's first tile. So no dependent load sits between
+        // two copies. A map word is a hint: a tile outside its item's tiles
+        // (a word left by another use of the workspace) is found by search.
+        constexpr int kWin = 4;  // window words per lane
+        struct Window {
+            uint32_t v[kWin];
+        };
         uint32_t issued = 0;
         bool stop = false;
-        auto item_of = [&](uint32_t jj) -> uint32_t {  // every lane: the item of tile jj, or 0 past the end
-            return jj < my_tiles ? *tile_item_at(L.status, b + jj * G) : 0u;
+        auto window = [&](uint32_t i) -> Window {  // this lane's words of the window after item i
+            Window w;
+#pragma unroll
+            for (int k = 0; k < kWin; ++k) {
+                const uint32_t j = i + 1u + uint32_t(lane) + 32u * k;
+                w.v[k] = j <= a.n_items && j > i ? L.tile_off[j] : 0xFFFFFFFFu;
+            }
+            return w;
+        };
+        auto resolve = [&](const Window &w, uint32_t i, uint32_t jj) -> uint32_t {  // item of tile jj (every lane)
+            if (jj >= my_tiles) return i;
+            const uint32_t t = b + jj * G;
+#pragma unroll
+            for (int k = 0; k < kWin; ++k) {
+                const uint32_t bal = __ballot_sync(kFull, w.v[k] > t);
+                if (bal) return i + 32u * k + uint32_t(__ffs(bal)) - 1u;
+            }
+            return find_item(L.tile_off, a.n_items, i + 32u * kWin, t);
         };
         auto record = [&](uint32_t i) -> uint32_t {  // this lane's word of item i's records
-            i = i < a.n_items ? i : 0u;                   // (a stale map cannot index past the items)
+            i = i < a.n_items ? i : 0u;
             if (lane < 12) return reinterpret_cast<const uint32_t *>(a.items + i)[lane];
             if (lane < 20) return reinterpret_cast<const uint32_t *>(L.plans + i)[lane - 12];
             return lane == 20 ? L.tile_off[i] : 0u;
         };
-        uint32_t idx1 = item_of(1), rec = record(item_of(0));
+        const uint32_t map_tag = epoch;  // the plan's epoch plus one: this launch's
+        auto map_of = [&](uint32_t jj) -> uint64_t {  // tile jj's map word (every lane)
+            return jj < my_tiles ? ld_relaxed_u64(tile_map_at(L.status, b + jj * G)) : 0ull;
+        };
+        auto mapped = [&](uint64_t m) { return uint32_t(m >> 32) == map_tag; };
+        const uint64_t m0 = map_of(0), m1 = map_of(1);
+        uint64_t m2 = map_of(2);
+        const uint32_t it0 = !my_tiles ? 0u : mapped(m0) ? uint32_t(m0) : find_item(L.tile_off, a.n_items, 0u, b);
+        uint32_t it1 = mapped(m1) ? uint32_t(m1) : resolve(window(it0), it0, 1u);  // item of tile jj + 1
+        Window win = window(it1);                                                // window after it
+        uint32_t rec = record(it0);
         for (uint32_t jj = 0; jj < my_tiles && !stop; ++jj) {
             const uint32_t tile = b + jj * G;
-            const uint32_t idx2 = item_of(jj + 2);
-            const uint32_t rec_next = jj + 1 < my_tiles ? record(idx1) : 0u;
+            const uint32_t it2 = mapped(m2) ? uint32_t(m2) : resolve(win, it1, jj + 2u);
+            m2 = map_of(jj + 3u);
+            const uint32_t rec_next = jj + 1 < my_tiles ? record(it1) : 0u;
+            if (jj + 2 < my_tiles) win = window(it2);
+            // a hint that does not hold: the item by search
+            if (tile - __shfl_sync(kFull, rec, 20) >= __shfl_sync(kFull, rec, 19))
+                rec = record(find_item(L.tile_off, a.n_items, 0u, tile));
             // tile jj's records from the lanes that hold them
             auto w = [&](int l) { return __shfl_sync(kFull, rec, l); };
             const uint64_t in_u = uint64_t(w(0)) | (uint64_t(w(1)) << 32);
@@ -153,7 +197,7 @@ __global__ void __launch_bounds__((CWW + 2) * 32, MINB) k_batch_tma(const BatchA
             }
             stop = __shfl_sync(kFull, stop ? 1u : 0u, 0) != 0u;
             rec = rec_next;
-            idx1 = idx2;
+            it1 = it2;
         }
         // Every copy has been consumed unless a wait gave up; wait (bounded)
         // for the last one on each stage so none lands after the block exits.

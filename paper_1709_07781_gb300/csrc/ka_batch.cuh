@@ -39,7 +39,8 @@ inline BatchLayout batch_layout(void *ws, uint64_t ws_bytes, uint32_t max_items)
     L.status = reinterpret_cast<uint64_t *>(p);
     const uint64_t fixed = batch_fixed_bytes(max_items);
     const uint64_t entries = ws_bytes > fixed ? (ws_bytes - fixed) / kStatusEntryBytes : 0;
-    L.status_cap = entries > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(entries);
+    // below 2^32 - 1: a saturated tile total (the plan's overflow mark) exceeds it
+    L.status_cap = entries > 0xFFFFFFFEull ? 0xFFFFFFFEu : uint32_t(entries);
     return L;
 }
 
@@ -72,11 +73,13 @@ __device__ __forceinline__ uint32_t find_item(const uint32_t *tile_off, uint32_t
 }
 
 #ifdef __CUDACC__
-// The item of flattened tile t, kept in the spare second word of the tile's
-// status entry (the first word is the tile's status); written by
-// k_batch_tile_items before the TMA batch kernel runs.
-__device__ __forceinline__ uint32_t *tile_item_at(uint64_t *status, uint32_t t) {
-    return reinterpret_cast<uint32_t *>(status + uint64_t(t) * 4u + 1u);
+// Map word of flattened tile t: (plan epoch << 32) | item, in the spare
+// second word of the tile's status entry (the first is the tile's status).
+// The plan kernel writes it for the tiles of small items; the TMA batch
+// kernel's producer reads it ahead and trusts it only under the plan epoch
+// of the same call.
+__device__ __forceinline__ uint64_t *tile_map_at(uint64_t *status, uint32_t t) {
+    return status + uint64_t(t) * 4u + 1u;
 }
 #endif
 

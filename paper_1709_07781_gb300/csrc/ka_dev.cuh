@@ -121,7 +121,7 @@ __host__ __device__ __forceinline__ uint32_t popc32(uint32_t x) {
 // Inverse of an odd d modulo 2^32 by Newton iteration: x <- x (2 - d x)
 // doubles the number of correct low bits each step, starting from x = d
 // (correct to 3 bits for odd d).
-__host__ __device__ inline uint32_t inverse_odd(uint32_t d) {
+__host__ __device__ __forceinline__ uint32_t inverse_odd(uint32_t d) {
     uint32_t x = d;
     for (int i = 0; i < 5; ++i) x *= 2u - d * x;
     return x;
@@ -129,7 +129,7 @@ __host__ __device__ inline uint32_t inverse_odd(uint32_t d) {
 
 // Canonical predicate for an API (kind, param): 0 on success, -1 for an
 // unknown kind or a zero modulus. Kind numbers are those of ka_pred_kind.
-__host__ __device__ inline int pred_canon(int32_t kind, uint32_t param, PredDev *out) {
+__host__ __device__ __forceinline__ int pred_canon(int32_t kind, uint32_t param, PredDev *out) {
     PredDev p{};
     switch (kind) {
     case 0: p.kind = kAndMaskEq0; p.a = param; break;  // KA_PRED_AND_MASK_EQ0

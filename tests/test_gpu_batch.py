@@ -133,6 +133,46 @@ def test_batch_in_place(ka, shape):
         assert np.array_equal(out[src.offs[i] + k: src.offs[i] + x.size], x[k:]), i
 
 
+@pytest.mark.parametrize("shape", [(128, 4)] + TMA_SHAPES)
+def test_batch_mostly_empty_items(ka, shape):
+    """Four empty items to each tiny one: G consecutive tiles then span far
+    more items than the producer's 128-item search window, so the item of a
+    tile is found by the full search, and empty items lie between the items
+    of consecutive tiles."""
+    sizes = [0 if i % 5 else 1 + (37 * i) % 900 for i in range(3000)] + [5000, 0, 0, 1]
+    xs = [ki.uniform_u32(4000 + i, n) for i, n in enumerate(sizes)]
+    preds = [PREDS[i % len(PREDS)] for i in range(len(xs))]
+    dst, counts, ws = run_batch(ka, xs, preds, tile=shape)
+    check(xs, preds, None, dst, counts)
+    assert ws.status(ka) == 0
+
+
+@pytest.mark.parametrize("shape", TMA_SHAPES)
+def test_batch_map_hints_are_checked(ka, shape):
+    """Every tile's map word carries the tag of the coming launch but names a
+    wrong item, as a word left by another use of the workspace might: the
+    plan rewrites the words of small items' tiles, and the producer checks
+    every other hint against the item's tiles and finds the item by search."""
+    sizes = [70000, 3, 12289, 0, 40001, 9000, 300001, 1, 513, 200000]
+    xs = [ki.uniform_u32(700 + i, n) for i, n in enumerate(sizes)]
+    preds = [PREDS[i % len(PREDS)] for i in range(len(xs))]
+    m = len(xs)
+    ws = Workspace(ka, sum(sizes) + 1, shape, batch_items=m)
+    ticket = int(ws.header_words()[0].item())
+    tag = ((ticket >> 32) + 1) & 0xFFFFFFFF  # the plan draws epoch E, the compaction kernel E + 1
+    r256 = lambda b: (b + 255) // 256 * 256  # noqa: E731
+    off = 256 + r256((m + 1) * 4) + r256(m * 32)  # header, tile offsets, plan records: then 32-byte entries
+    base = ws.ptr - ws.buf.data_ptr() + off
+    n_entries = (ws.nbytes - off) // 32
+    rng = np.random.default_rng(3)
+    hints = (np.uint64(tag) << np.uint64(32)) | rng.integers(0, m, n_entries).astype(np.uint64)
+    words = ws.buf[base: base + 32 * n_entries].view(torch.int64).view(n_entries, 4)
+    words[:, 1] = torch.from_numpy(hints.view(np.int64)).to(words.device)
+    dst, counts, _ = run_batch(ka, xs, preds, tile=shape, ws=ws)
+    check(xs, preds, None, dst, counts)
+    assert ws.status(ka) == 0
+
+
 @pytest.mark.parametrize("shape", [(128, 4), (768, 16)])
 def test_batch_many_tiny_instances(ka, shape):
     """Thousands of one-tile items: the item search jumps far between tiles."""
