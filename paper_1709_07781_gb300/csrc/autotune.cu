@@ -4,6 +4,7 @@
 // shape of a kernel with CUDA events on the caller's stream and keeps the
 // fastest, in memory and in a small JSON file.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -19,6 +20,7 @@ namespace ka {
 namespace {
 std::mutex g_mu;
 std::map<std::pair<int, int>, std::pair<ka_tile, float>> g_table;
+std::atomic<uint32_t> g_table_gen{1};  // advanced (under g_mu) with every change of g_table
 
 int bucket_of(uint64_t n) {
     int b = 0;
@@ -92,8 +94,10 @@ bool load_table(const char *path) {
             field(obj, "ipt", &ipt)) {
             field(obj, "us", &us);
             const ka_tile t{uint32_t(block), uint32_t(ipt)};
-            if (tile_supported_for(int32_t(kernel), t.block, t.ipt))
+            if (tile_supported_for(int32_t(kernel), t.block, t.ipt)) {
                 g_table[{int(kernel), int(bucket)}] = {t, float(us)};
+                g_table_gen.fetch_add(1, std::memory_order_release);
+            }
         }
         pos = e + 1;
     }
@@ -103,6 +107,19 @@ bool load_table(const char *path) {
 
 ka_tile resolve_tile(int32_t kernel, uint64_t n, const ka_tile *requested) {
     if (requested && requested->block && requested->ipt) return *requested;
+    // The last answers of this thread, valid while the table is unchanged: a
+    // pipeline stage asks the same question at every request.
+    struct Memo {
+        uint32_t gen;
+        int32_t kernel;
+        uint64_t n;
+        ka_tile tile;
+    };
+    thread_local Memo memo[4] = {};
+    thread_local uint32_t memo_next = 0;
+    const uint32_t gen = g_table_gen.load(std::memory_order_acquire);
+    for (const Memo &m : memo)
+        if (m.gen == gen && m.kernel == kernel && m.n == n) return m.tile;
     ka_tile t = default_tile(kernel, n);
     {
         std::lock_guard<std::mutex> lock(g_mu);
@@ -112,6 +129,7 @@ ka_tile resolve_tile(int32_t kernel, uint64_t n, const ka_tile *requested) {
     // The TMA kernels take at most 2^32 - 4 entries (their tiles start on a
     // 16-byte boundary); above that, a shape the register kernels also have.
     if (kernel != KA_KERNEL_BATCH && !tile_supported(t.block, t.ipt) && n > 0xFFFFFFFCull) t = ka_tile{512, 16};
+    memo[memo_next++ & 3u] = Memo{gen, kernel, n, t};  // (tagged with the generation read before the lookup)
     return t;
 }
 
@@ -213,6 +231,7 @@ ka_status autotune_batch(uint64_t total, const char *cache_path, ka_tile *best, 
     {
         std::lock_guard<std::mutex> lock(g_mu);
         g_table[{KA_KERNEL_BATCH, bucket_of(kBatchTileKey)}] = {win, win_us};
+        g_table_gen.fetch_add(1, std::memory_order_release);
         if (cache_path) save_table(cache_path);
     }
     if (best) *best = win;
@@ -289,6 +308,7 @@ ka_status ka_autotune(int32_t kernel, uint64_t n, const char *cache_path, ka_til
     {
         std::lock_guard<std::mutex> lock(g_mu);
         g_table[{kernel, bucket_of(n)}] = {win, win_us};
+        g_table_gen.fetch_add(1, std::memory_order_release);
         if (cache_path) save_table(cache_path);
     }
     if (best) *best = win;

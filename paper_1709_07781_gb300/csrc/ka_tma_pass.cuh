@@ -110,7 +110,12 @@ __device__ __forceinline__ void tma_produce(const TmaArgs &a, uint32_t *stage_me
         }
         fence_proxy_async();  // the compute warps' accesses to this stage precede the copy into it
         mbar_expect_tx(&full_bar[s], uint32_t(T) * 4u);
-        bulk_g2s(stage_mem + size_t(s) * T, a.in + size_t(tile) * T, uint32_t(T) * 4u, &full_bar[s]);
+        // two copies of half a tile each, both completing on the stage's
+        // barrier (measured 0.5 % faster than one at 1 % and 50 % kept)
+        static_assert(T % 8 == 0, "each half is whole 16-byte chunks");
+        bulk_g2s(stage_mem + size_t(s) * T, a.in + size_t(tile) * T, uint32_t(T / 2) * 4u, &full_bar[s]);
+        bulk_g2s(stage_mem + size_t(s) * T + T / 2, a.in + size_t(tile) * T + T / 2, uint32_t(T / 2) * 4u,
+                 &full_bar[s]);
         issued = jj + 1;
     }
     for (uint32_t jj = issued > uint32_t(S) ? issued - S : 0u; jj < issued; ++jj)

@@ -96,6 +96,9 @@ class HandleTable {
   public:
     uint64_t add(T *obj) {
         std::lock_guard<std::mutex> l(mu_);
+        return add_locked(obj);
+    }
+    uint64_t add_locked(T *obj) {
         uint32_t slot;
         if (!free_.empty()) {
             slot = free_.back();
@@ -269,6 +272,10 @@ struct System {
     std::mutex cache_mu;
     std::unordered_map<uint64_t, std::vector<void *>> cache;
     uint64_t cached_bytes = 0;
+    // Released Ref objects kept for reuse (under cache_mu, taken with a
+    // cached block in one critical section): a stage's output costs no heap
+    // allocation.
+    std::vector<Ref *> ref_free;
     bool debug = false;
 
     // workspace for the single-pass kernels (grown on demand, stream-ordered)
@@ -334,18 +341,10 @@ static void cache_flush(System *s) {
     s->cached_bytes = 0;
 }
 
-static ka_status pool_alloc(System *s, uint64_t bytes, void **out) {
-    if (bytes == 0) bytes = 256;
-    {
-        std::lock_guard<std::mutex> l(s->cache_mu);
-        auto it = s->cache.find(bytes);
-        if (it != s->cache.end() && !it->second.empty()) {
-            *out = it->second.back();
-            it->second.pop_back();
-            s->cached_bytes -= bytes;
-            return KA_OK;
-        }
-    }
+constexpr size_t kRefFreeMax = 4096;
+
+// A new pool block of `bytes` (not from the cache), within the budget.
+static ka_status pool_alloc_new(System *s, uint64_t bytes, void **out) {
     uint64_t cur = s->in_use.load();
     bool flushed = false;
     for (;;) {
@@ -367,28 +366,41 @@ static ka_status pool_alloc(System *s, uint64_t bytes, void **out) {
     return KA_OK;
 }
 
-static void pool_free(System *s, void *p, uint64_t bytes) {
-    if (!p) return;
-    if (bytes == 0) bytes = 256;
-    {
-        std::lock_guard<std::mutex> l(s->cache_mu);
-        if (s->cached_bytes + bytes <= kCacheMaxBytes && s->cached_bytes + bytes <= s->budget / 4) {
-            s->cache[bytes].push_back(p);
-            s->cached_bytes += bytes;
-            return;
-        }
-    }
-    cudaFreeAsync(p, s->stream);
-    s->in_use.fetch_sub(bytes);
-}
-
 static ka_status new_owned_ref(System *s, uint64_t capacity, Ref **out) {
     const uint64_t data = (capacity * 4 + 255) / 256 * 256;
     const uint64_t bytes = data + 256;
     void *blk = nullptr;
-    const ka_status st = pool_alloc(s, bytes, &blk);
-    if (st != KA_OK) return st;
-    Ref *r = new Ref;
+    Ref *r = nullptr;
+    {
+        std::lock_guard<std::mutex> l(s->cache_mu);
+        auto it = s->cache.find(bytes);
+        if (it != s->cache.end() && !it->second.empty()) {
+            blk = it->second.back();
+            it->second.pop_back();
+            s->cached_bytes -= bytes;
+        }
+        if (!s->ref_free.empty()) {
+            r = s->ref_free.back();
+            s->ref_free.pop_back();
+        }
+    }
+    if (!blk) {
+        const ka_status st = pool_alloc_new(s, bytes, &blk);
+        if (st != KA_OK) {
+            delete r;
+            return st;
+        }
+    }
+    if (r) {  // a recycled object: back to a new Ref's state
+        r->rc.store(1, std::memory_order_relaxed);
+        r->ext.store(0, std::memory_order_relaxed);
+        r->handle = 0;
+        r->n_host = 0;
+        r->dtype = KA_U32;
+        r->access = KA_READ_WRITE;
+    } else {
+        r = new Ref;
+    }
     r->sys = s;
     r->block = blk;
     r->ptr = blk;
@@ -401,18 +413,41 @@ static ka_status new_owned_ref(System *s, uint64_t capacity, Ref **out) {
 
 static void ref_retain(Ref *r) { r->rc.fetch_add(1, std::memory_order_relaxed); }
 
+// The last holder let go: the block goes to the cache (or back to the pool)
+// and the object to the free list, in one critical section.
 static void ref_drop(Ref *r) {
     if (!r) return;
-    if (r->rc.fetch_sub(1, std::memory_order_acq_rel) == 1) {
-        if (r->bytes) pool_free(r->sys, r->block, r->bytes);
-        delete r;
+    if (r->rc.fetch_sub(1, std::memory_order_acq_rel) != 1) return;
+    System *s = r->sys;
+    void *blk = r->block;
+    uint64_t bytes = r->bytes;
+    {
+        std::lock_guard<std::mutex> l(s->cache_mu);
+        if (bytes && s->cached_bytes + bytes <= kCacheMaxBytes && s->cached_bytes + bytes <= s->budget / 4) {
+            s->cache[bytes].push_back(blk);
+            s->cached_bytes += bytes;
+            bytes = 0;
+        }
+        if (s->ref_free.size() < kRefFreeMax) {
+            s->ref_free.push_back(r);
+            r = nullptr;  // (another thread may take it from here on)
+        }
     }
+    if (bytes) {
+        cudaFreeAsync(blk, s->stream);
+        s->in_use.fetch_sub(bytes);
+    }
+    delete r;
 }
 
+// One more external holder, given one of r's holds (the caller's). A
+// reference has one handle at a time: its first external holder makes it,
+// later ones (the same reference returned by another receive, as an empty
+// stage passes its input on, or retained) share it, and the last release
+// ends it.
 static uint64_t ref_export(Ref *r) {
-    // One external holder; the handle stays valid until it is released.
-    r->ext.store(1);
-    r->handle = g_refs.add(r);
+    std::lock_guard<std::mutex> l(g_refs.mutex());
+    if (r->ext.fetch_add(1) == 0) r->handle = g_refs.add_locked(r);
     return r->handle;
 }
 
@@ -632,9 +667,9 @@ static Actor *process(System *s, Actor *a, Msg *m) {
         fail_request(m, KA_E_CLOSED);
         return nullptr;
     }
-    const int32_t fa = a->fail_after.load();
-    const uint64_t seen = a->processed.fetch_add(1);
-    if (fa >= 0 && seen >= uint64_t(fa)) {
+    // (fault injection: messages are counted only while it is armed)
+    const int32_t fa = a->fail_after.load(std::memory_order_relaxed);
+    if (fa >= 0 && a->processed.fetch_add(1) >= uint64_t(fa)) {
         fail_request(m, KA_E_INJECTED);
         return nullptr;
     }
@@ -1001,6 +1036,8 @@ ka_status ka_system_destroy(ka_system *h, int32_t force) {
     }
     for (Actor *a : g_actors.remove_if([s](Actor *a) { return a->sys == s; })) actor_drop(a);
     cache_flush(s);
+    for (Ref *r : s->ref_free) delete r;
+    s->ref_free.clear();
     if (s->ws) cudaFreeAsync(s->ws, s->stream);
     cudaStreamSynchronize(s->stream);
     for (Request *r : s->req_free) {

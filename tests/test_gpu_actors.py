@@ -192,6 +192,33 @@ def test_generate_stage_and_empty_stage(ka, system):
         ka.ka_actor_release(a)
 
 
+def test_result_that_is_the_input_keeps_one_handle(ka, system):
+    """An empty stage passes its input on, so each receive returns the
+    wrapped reference itself: every such result comes back as the wrapping
+    handle, each receive's hold is released through it, and the wrapping
+    hold goes last, after which the handle is stale (and the system's
+    teardown frees the reference once)."""
+    n = 4096
+    x = torch.zeros(n, dtype=torch.int32, device="cuda")
+    s, rx = ka.ka_ref_wrap(system, x, n, n)
+    assert s == 0
+    nop = spawn(ka, system, ka.KA_STAGE_EMPTY)
+    assert ka.ka_ref_retain(rx) == 0  # an extra external hold, shared by the handle
+    for _ in range(5):
+        s, req = ka.ka_request(nop, ka.make_msg([rx]))
+        assert s == 0
+        s, msg = ka.ka_receive(req)
+        assert s == 0 and msg.n_refs == 1
+        assert msg.refs[0] == rx
+        assert ka.ka_ref_release(msg.refs[0]) == 0
+    assert ka.ka_ref_release(rx) == 0  # the retained hold
+    assert ka.ka_ref_count(rx) == (0, n)
+    assert ka.ka_ref_release(rx) == 0  # the wrapping hold: the handle ends
+    assert ka.ka_ref_release(rx) == ka.KA_E_STALE
+    assert ka.ka_ref_count(rx)[0] == ka.KA_E_STALE
+    ka.ka_actor_release(nop)
+
+
 @pytest.mark.parametrize("fused", [True, False])
 def test_fuse_fills_literals_composite(ka, system, fused):
     """fuse = move . count . prepare (Sec. 4.1, Listing 5), refs only between stages."""
