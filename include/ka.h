@@ -98,12 +98,12 @@ typedef enum ka_pred_kind {
 
 /* Tile shape of a tiled kernel: threads per block and items per thread.
  * Supported: block 128, 256 or 512 with ipt 4, 8 or 16, block 1024 with ipt
- * 4 or 8, and (768, 16). The shapes (256, 16), (512, 16) and (768, 16)
- * select the warp-specialised TMA kernels (compaction, scan, batch): compute
- * warps of 512 entries each, plus a look-back warp and a producer warp; block
- * / 32 compute warps, except that the compaction and the scan of (768, 16)
- * have 26 (tiles of 13312 entries; its batch kernel has 24). A tile holds 512
- * to 13312 entries.
+ * 4 or 8, and (768, 16); the batch kernel also takes (704, 16). The shapes
+ * (256, 16), (512, 16), (704, 16) and (768, 16) select the warp-specialised
+ * TMA kernels (compaction, scan, batch): compute warps of 512 entries each,
+ * plus a look-back warp and a producer warp; block / 32 compute warps, except
+ * that the compaction and the scan of (768, 16) have 26 (tiles of 13312
+ * entries; its batch kernel has 24). A tile holds 512 to 13312 entries.
  * A NULL tile, or {0, 0}, picks the library default (or the autotuned shape
  * once ka_autotune has run for that kernel). */
 typedef struct ka_tile {

@@ -36,10 +36,12 @@ const ka_tile kShapes[] = {
 
 // The TMA kernels (compaction, scan, batch) also have the shape (768, 16).
 const ka_tile kTmaOnlyShapes[] = {{768, 16}};
+// The batch kernel also has (704, 16), its default.
+const ka_tile kBatchOnlyShapes[] = {{704, 16}};
 
 ka_tile default_tile(int32_t kernel, uint64_t n) {
     if (kernel == KA_KERNEL_COMPACT && n >= (1ull << 22)) return ka_tile{768, 16};  // TMA kernel
-    if (kernel == KA_KERNEL_BATCH) return ka_tile{512, 16};                         // TMA batch kernel
+    if (kernel == KA_KERNEL_BATCH) return ka_tile{704, 16};                         // TMA batch kernel
     if (kernel == KA_KERNEL_SCAN && n >= (1ull << 22)) return ka_tile{512, 16};      // TMA kernel, scan mode
     if (n >= (1ull << 24)) return ka_tile{256, 16};
     if (n >= (1ull << 21)) return ka_tile{256, 8};
@@ -208,6 +210,7 @@ ka_status autotune_batch(uint64_t total, const char *cache_path, ka_tile *best, 
     if (s == KA_OK) {
         std::vector<ka_tile> shapes(std::begin(kShapes), std::end(kShapes));
         shapes.insert(shapes.end(), std::begin(kTmaOnlyShapes), std::end(kTmaOnlyShapes));
+        shapes.insert(shapes.end(), std::begin(kBatchOnlyShapes), std::end(kBatchOnlyShapes));
         for (const ka_tile &t : shapes) {
             auto launch = [&]() -> ka_status { return ka_compact_batch(d_items, m, m, ws, ws_bytes, &t, 0, st); };
             const float us = time_launches(launch, st, 2, 9);

@@ -52,6 +52,7 @@ bool tile_supported(uint32_t block, uint32_t ipt) {
 }
 
 bool tile_supported_for(int32_t kernel, uint32_t block, uint32_t ipt) {
+    if (kernel == KA_KERNEL_BATCH) return tile_supported(block, ipt) || batch_tma_shape(block, ipt);
     return tile_supported(block, ipt) || tma_shape(block, ipt);  // every kernel has the TMA shapes
 }
 

@@ -380,7 +380,7 @@ ka_status ka_compact_batch(const ka_batch_item *d_items, uint32_t n_items, uint3
     a.n_items = n_items;
     a.L = batch_layout(d_ws, ws_bytes, max_items);
     a.ws = static_cast<WsHeader *>(d_ws);
-    const bool tma = tma_shape(t.block, t.ipt);
+    const bool tma = batch_tma_shape(t.block, t.ipt);
     // one plan block per 256 items, each with a status word of its own
     const uint32_t plan_blocks = (n_items + kBatchPlanBlock - 1) / kBatchPlanBlock;
     if (plan_blocks > a.L.status_cap) return KA_E_WORKSPACE;

@@ -61,6 +61,8 @@ bool tile_supported(uint32_t block, uint32_t ipt);
 // Shapes of the warp-specialised TMA kernels (compaction, scan, batch):
 // (256, 16), (512, 16) and (768, 16); the last exists for them only.
 bool tma_shape(uint32_t block, uint32_t ipt);
+// Shape of the TMA batch kernel: the TMA shapes and (704, 16).
+bool batch_tma_shape(uint32_t block, uint32_t ipt);
 // Shape valid for `kernel` (a KA_KERNEL_* id).
 bool tile_supported_for(int32_t kernel, uint32_t block, uint32_t ipt);
 // Shape to use for `kernel` at size n: explicit shape, else autotuned, else default.

@@ -993,6 +993,10 @@ ka_status ka_system_create(const ka_config *cfg, ka_system **out) {
         delete s;
         return st;
     }
+    // Zero every slot: a completion tag of 0 is never issued, while pinned
+    // memory comes back uncleared (a slot of a destroyed system could still
+    // hold the tag a new request is about to wait for).
+    std::memset(s->pinned, 0, size_t(kPinnedSlots) * kPinnedWords * 4);
     s->pin_free.reserve(kPinnedSlots);
     for (uint32_t i = kPinnedSlots; i-- > 0;) s->pin_free.push_back(i);
     if (cfg && cfg->autotune_cache) ka_autotune_load(cfg->autotune_cache);

@@ -77,7 +77,7 @@ def test_workspace_size(ka):
 def test_default_tiles(ka):
     assert ka.ka_tile_for(ka.KA_KERNEL_COMPACT, 1 << 28) == (0, (768, 16))
     assert ka.ka_tile_for(ka.KA_KERNEL_SCAN, 1 << 28) == (0, (512, 16))
-    assert ka.ka_tile_for(ka.KA_KERNEL_BATCH, 1 << 17) == (0, (512, 16))
+    assert ka.ka_tile_for(ka.KA_KERNEL_BATCH, 1 << 17) == (0, (704, 16))
     s, t = ka.ka_tile_for(ka.KA_KERNEL_COMPACT, 1 << 20)
     assert s == 0 and t[0] * t[1] <= 4096
 

@@ -219,6 +219,32 @@ def test_result_that_is_the_input_keeps_one_handle(ka, system):
     ka.ka_actor_release(nop)
 
 
+def test_new_systems_do_not_see_old_completion_tags(ka):
+    """Systems made and destroyed in turn, one request each: every first
+    request waits for completion tag 1 in its slot, which a destroyed
+    system's slot (pinned memory is handed back uncleared) would already
+    hold. Each result must still be the real one."""
+    n = (1 << 20) + 7
+    x = ki.uniform_u32(31, n)
+    d_x = to_dev(x)
+    _, k = oracle.compact(x, "lt", ki.threshold_for(0.3))
+    for _ in range(12):
+        s, sys_h = ka.ka_system_create(0)
+        assert s == 0
+        comp = spawn(ka, sys_h, ka.KA_STAGE_COMPACT, ka.KA_PRED_LT, ki.threshold_for(0.3))
+        s, rx = ka.ka_ref_wrap(sys_h, d_x, n, n)
+        assert s == 0
+        s, req = ka.ka_request(comp, ka.make_msg([rx]))
+        assert s == 0
+        s, msg = ka.ka_receive(req)
+        assert s == 0 and msg.count == k
+        for i in range(msg.n_refs):
+            ka.ka_ref_release(msg.refs[i])
+        ka.ka_ref_release(rx)
+        ka.ka_actor_release(comp)
+        assert ka.ka_system_destroy(sys_h, 1) == 0
+
+
 @pytest.mark.parametrize("fused", [True, False])
 def test_fuse_fills_literals_composite(ka, system, fused):
     """fuse = move . count . prepare (Sec. 4.1, Listing 5), refs only between stages."""

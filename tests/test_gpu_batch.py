@@ -87,7 +87,7 @@ PREDS = [("lt", ki.threshold_for(0.3)), ("and_mask_eq0", 3), ("popc_odd", 0), ("
          ("ne", 0), ("all", 0)]
 
 
-TMA_SHAPES = [(768, 16), (512, 16), (256, 16)]
+TMA_SHAPES = [(768, 16), (704, 16), (512, 16), (256, 16)]
 
 
 @pytest.mark.parametrize("shape", [(128, 4), (256, 8), (512, 8), (128, 16)] + TMA_SHAPES)
