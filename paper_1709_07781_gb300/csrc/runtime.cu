@@ -238,23 +238,34 @@ struct Request {
     std::condition_variable cv;
     std::atomic<bool> done{false};
     bool debug_check = false;
-    // holders: the caller's handle, plus the completion queue once the last
-    // stage has been issued; the last holder frees the request
+    // holders: the caller's handle; the last holder recycles the request
     std::atomic<int> holders{1};
     std::atomic<bool> recorded{false};  // event recorded after the last stage
     std::atomic<bool> blocked{false};   // a receiver is (about to be) blocked on cv
-    // The two flags the completion thread watches while a receiver polls, on
+    // The two words the completion thread watches while a receiver polls, on
     // a cache line of their own: the fulfilling receiver's writes to the
     // result fields above then do not contend with the watcher's reads.
-    alignas(64) std::atomic<bool> claimed{false};  // a thread has taken on fulfilling the promise
-    std::atomic<bool> waiting{false};              // a receiver is polling for completion
-    char pad_[62];
+    // claim = (use << 1) | taken: one thread per use fulfils the request.
+    // Recycling starts the next use unclaimed, so the completion queue's
+    // entry for an earlier use (which holds no reference) cannot claim it.
+    alignas(64) std::atomic<uint64_t> claim{0};
+    std::atomic<bool> waiting{false};  // a receiver is polling for completion
+    char pad_[55];
 };
 
-
+// A request of the completion queue: the object (kept while its system
+// lives) and the use the entry is for.
 struct Completion {
     Request *req;
+    uint64_t use;
 };
+
+static bool try_claim(Request *r, uint64_t use) {
+    uint64_t open = use << 1;
+    return r->claim.compare_exchange_strong(open, open | 1u, std::memory_order_acq_rel);
+}
+static uint64_t current_use(const Request *r) { return r->claim.load(std::memory_order_acquire) >> 1; }
+static bool is_claimed(const Request *r) { return (r->claim.load(std::memory_order_acquire) & 1u) != 0; }
 
 struct System {
     int device = 0;
@@ -719,15 +730,16 @@ static Actor *process(System *s, Actor *a, Msg *m) {
     if (pub == KA_OK && rec == cudaSuccess) rec = cudaEventRecord(r->event, s->stream);
     if (pub != KA_OK || rec != cudaSuccess) {
         if (rec != cudaSuccess) cudaGetLastError();
-        r->claimed.store(true);
+        r->claim.fetch_or(1u, std::memory_order_acq_rel);
         complete(r, pub != KA_OK ? pub : cuda_status(rec));
         return nullptr;
     }
-    r->holders.fetch_add(1, std::memory_order_relaxed);  // the completion queue's hold
     r->recorded.store(true, std::memory_order_release);
     {
+        // (no reference: the caller's hold keeps the object; its use number
+        // tells the completion thread whether the entry is still current)
         std::lock_guard<std::mutex> l(s->comp_mu);
-        s->comp_q.push_back({r});
+        s->comp_q.push_back({r, current_use(r)});
     }
     s->comp_pushed.fetch_add(1, std::memory_order_release);
     s->comp_cv.notify_one();
@@ -828,8 +840,6 @@ static void finalize(System *s, Request *r, ka_status st) {
     complete(r, st);
 }
 
-static void request_unhold(Request *r);
-
 static void completer_main(System *s) {
     cudaSetDevice(s->device);
     uint64_t taken = 0;
@@ -851,17 +861,19 @@ static void completer_main(System *s) {
             ++taken;
         }
         Request *r = c.req;
-        // A receiver polling r fulfils it itself; this thread stays out of the
-        // driver meanwhile and steps in only once no receiver is polling.
-        // (checked every 20 us: a polling receiver claims its request within
-        // microseconds, and a tighter watch only costs it coherence misses)
-        while (!r->claimed.load(std::memory_order_acquire) && r->waiting.load(std::memory_order_acquire))
+        const uint64_t open = c.use << 1;  // the entry's use, not yet claimed
+        // A receiver polling r fulfils it itself (and may have received and
+        // reused it already: the claim word then reads otherwise); this
+        // thread stays out of the driver meanwhile and steps in only once no
+        // receiver is polling. (Checked every 20 us: a polling receiver
+        // claims its request within microseconds, and a tighter watch only
+        // costs it coherence misses.)
+        while (r->claim.load(std::memory_order_acquire) == open && r->waiting.load(std::memory_order_acquire))
             std::this_thread::sleep_for(std::chrono::microseconds(20));
-        if (!r->claimed.load(std::memory_order_acquire)) {
+        if (r->claim.load(std::memory_order_acquire) == open) {
             const ka_status st = cuda_status(cudaEventSynchronize(r->event));
-            if (!r->claimed.exchange(true, std::memory_order_acq_rel)) finalize(s, r, st);
+            if (try_claim(r, c.use)) finalize(s, r, st);
         }
-        request_unhold(r);
     }
 }
 
@@ -917,7 +929,7 @@ static void request_recycle(Request *r) {
     r->done.store(false, std::memory_order_relaxed);
     r->holders.store(1, std::memory_order_relaxed);
     r->recorded.store(false, std::memory_order_relaxed);
-    r->claimed.store(false, std::memory_order_relaxed);
+    r->claim.store(((r->claim.load(std::memory_order_relaxed) >> 1) + 1u) << 1, std::memory_order_release);
     r->waiting.store(false, std::memory_order_relaxed);
     r->blocked.store(false, std::memory_order_relaxed);
     System *s = r->sys;
@@ -1366,18 +1378,18 @@ ka_status ka_receive(ka_request_h *h, int64_t timeout_ns, ka_msg *out) {
                               ? std::chrono::nanoseconds(timeout_ns)
                               : std::chrono::nanoseconds(int64_t(kReceiveSpinUs) * 1000);
         while (!r->done.load(std::memory_order_acquire) && std::chrono::steady_clock::now() - t0 < spin) {
-            if (!r->recorded.load(std::memory_order_acquire) || r->claimed.load(std::memory_order_acquire)) continue;
+            if (!r->recorded.load(std::memory_order_acquire) || is_claimed(r)) continue;
             if (r->tagged) {
                 // the publish kernel's tag: every stage has finished (a failed
                 // launch never stores it; the completion thread reports that)
                 if (__atomic_load_n(&r->pinned_count[2], __ATOMIC_ACQUIRE) != r->seq) continue;
-                if (!r->claimed.exchange(true, std::memory_order_acq_rel)) finalize(s, r, KA_OK);
+                if (try_claim(r, current_use(r))) finalize(s, r, KA_OK);
                 continue;
             }
             const cudaError_t q = cudaEventQuery(r->event);
             if (q == cudaErrorNotReady) continue;
             if (q != cudaSuccess) cudaGetLastError();
-            if (!r->claimed.exchange(true, std::memory_order_acq_rel)) finalize(s, r, cuda_status(q));
+            if (try_claim(r, current_use(r))) finalize(s, r, cuda_status(q));
         }
         r->waiting.store(false, std::memory_order_release);
         if (!r->done.load(std::memory_order_acquire)) {
