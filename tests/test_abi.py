@@ -82,6 +82,26 @@ def test_default_tiles(ka):
     assert s == 0 and t[0] * t[1] <= 4096
 
 
+def test_batch_only_shape(ka, tmp_path):
+    """(704, 16) is a shape of the batch kernel (five stages) and of no other:
+    a batch workspace takes it, a single-array workspace refuses it, and a
+    tuning cache entry naming it is taken for the batch kernel and skipped
+    for the compaction."""
+    s, nbytes = ka.ka_batch_workspace_size(16, 1 << 20, (704, 16))
+    assert s == 0 and nbytes > 0
+    s, _ = ka.ka_workspace_size(1 << 20, (704, 16))
+    assert s == ka.KA_E_ARG
+    assert ka.ka_batch_workspace_size(16, 1 << 20, (640, 16))[0] == ka.KA_E_ARG
+    before = ka.ka_tile_for(ka.KA_KERNEL_COMPACT, 1 << 30)
+    p = tmp_path / "tune.json"
+    p.write_text('{"entries": [\n  {"kernel": %d, "bucket": 30, "block": 704, "ipt": 16, "us": 1.0},\n'
+                 '  {"kernel": %d, "bucket": 17, "block": 704, "ipt": 16, "us": 1.0}\n]}\n'
+                 % (ka.KA_KERNEL_COMPACT, ka.KA_KERNEL_BATCH))
+    assert ka.ka_autotune_load(str(p)) == 0
+    assert ka.ka_tile_for(ka.KA_KERNEL_COMPACT, 1 << 30) == before
+    assert ka.ka_tile_for(ka.KA_KERNEL_BATCH, 1 << 17) == (0, (704, 16))
+
+
 def test_autotune_cache_roundtrip(ka, tmp_path):
     p = tmp_path / "tune.json"
     p.write_text('{"entries": [\n  {"kernel": 0, "bucket": 17, "block": 128, "ipt": 8, "us": 3.5}\n]}\n')
