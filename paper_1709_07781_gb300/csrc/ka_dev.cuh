@@ -257,6 +257,9 @@ __device__ __forceinline__ uint64_t *status_at(uint64_t *status, uint64_t idx) {
     return status + idx * kStatusStride;
 }
 
+// Brings the sector holding *p into L2 ahead of its first use.
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // ---------------------------------------------------------------------------
 // Decoupled look-back, run by one full warp for tile `tile` whose first tile
 // of its segment is `first_tile` (0 for a single array; the first tile of

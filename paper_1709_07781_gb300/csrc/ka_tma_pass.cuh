@@ -108,6 +108,10 @@ __device__ __forceinline__ void tma_produce(const TmaArgs &a, uint32_t *stage_me
             record_error(a.ws, kDevErrTimeout, tile);
             break;
         }
+        // the status sector of this block's tile two ahead: in L2 before its
+        // aggregate is stored and polled (first touches by those went to
+        // DRAM; 1 % faster at s = 1 %)
+        if (jj + 2 < my_tiles) prefetch_l2(status_at(a.status, uint64_t(tile) + 2u * G));
         fence_proxy_async();  // the compute warps' accesses to this stage precede the copy into it
         mbar_expect_tx(&full_bar[s], uint32_t(T) * 4u);
         // two copies of half a tile each, both completing on the stage's

@@ -319,7 +319,7 @@ struct System {
     std::mutex comp_mu;
     std::condition_variable comp_cv;
     std::deque<Completion> comp_q;
-    std::atomic<uint64_t> comp_pushed{0};  // completions queued so far (for the completer's spin)
+    bool comp_kick = false;  // (under comp_mu) a receiver about to block, or shutdown: sweep now
     std::thread completer;
 
     std::atomic<int64_t> inflight{0};
@@ -734,15 +734,24 @@ static Actor *process(System *s, Actor *a, Msg *m) {
         complete(r, pub != KA_OK ? pub : cuda_status(rec));
         return nullptr;
     }
+    // The use is read before `recorded` is set: from then on a polling
+    // receiver may fulfil the request and its caller recycle it.
+    const uint64_t use = current_use(r);
     r->recorded.store(true, std::memory_order_release);
+    bool kick = false;
     {
         // (no reference: the caller's hold keeps the object; its use number
         // tells the completion thread whether the entry is still current)
         std::lock_guard<std::mutex> l(s->comp_mu);
-        s->comp_q.push_back({r, current_use(r)});
+        s->comp_q.push_back({r, use});
+        // A receiver that blocked before this push found no entry to sweep:
+        // wake the thread for it. (It sets `blocked` before it kicks, and
+        // both sides hold comp_mu, so one of the two sweeps sees the entry.)
+        if (r->blocked.load(std::memory_order_acquire)) kick = s->comp_kick = true;
     }
-    s->comp_pushed.fetch_add(1, std::memory_order_release);
-    s->comp_cv.notify_one();
+    // (otherwise no wake-up: the completion thread sweeps its queue every
+    // kCompleterPeriodUs, and a receiver that stops polling wakes it)
+    if (kick) s->comp_cv.notify_one();
     return nullptr;
 }
 
@@ -774,6 +783,7 @@ static void drain_with(System *s, ka_status st) {
 // Host-side spin windows (microseconds) before a thread blocks: a blocked
 // thread costs a futex wake-up (several microseconds) when work arrives.
 constexpr int kDispatcherSpinUs = 2000;
+constexpr int kCompleterPeriodUs = 2000;
 constexpr int kReceiveSpinUs = 2000;
 
 static void dispatcher_main(System *s) {
@@ -840,40 +850,55 @@ static void finalize(System *s, Request *r, ka_status st) {
     complete(r, st);
 }
 
+// Wakes the completion thread for a sweep now.
+static void kick_completer(System *s) {
+    {
+        std::lock_guard<std::mutex> l(s->comp_mu);
+        s->comp_kick = true;
+    }
+    s->comp_cv.notify_one();
+}
+
+// The completion thread sweeps its queue every kCompleterPeriodUs (100 us
+// once the system is stopping), or at once when kicked. An entry whose use is
+// fulfilled (and maybe reused: the claim word then reads otherwise) is
+// dropped; one whose receiver is polling is kept for a later sweep (that
+// receiver fulfils it itself, and the thread stays out of the driver and off
+// the request's cache lines meanwhile); any other is fulfilled here once its
+// event completes. Requests do not wake the thread, so a request/receive loop
+// leaves it asleep.
 static void completer_main(System *s) {
     cudaSetDevice(s->device);
-    uint64_t taken = 0;
+    std::deque<Completion> mine;
     for (;;) {
-        Completion c;
         {
-            // spin briefly for the next completion before blocking on the queue
-            const auto t0 = std::chrono::steady_clock::now();
-            while (s->comp_pushed.load(std::memory_order_acquire) == taken && !s->stop.load() &&
-                   std::chrono::steady_clock::now() - t0 < std::chrono::microseconds(kDispatcherSpinUs))
-                std::this_thread::yield();
             std::unique_lock<std::mutex> l(s->comp_mu);
-            while (s->comp_q.empty()) {
-                if (s->stop.load() && s->inflight.load() <= 0) return;
-                s->comp_cv.wait_for(l, std::chrono::microseconds(500));
+            if (!s->comp_kick) {
+                const auto period = std::chrono::microseconds(s->stop.load() ? 100 : kCompleterPeriodUs);
+                s->comp_cv.wait_for(l, period, [s] { return s->comp_kick; });
             }
-            c = s->comp_q.front();
-            s->comp_q.pop_front();
-            ++taken;
+            s->comp_kick = false;
+            while (!s->comp_q.empty()) {
+                mine.push_back(s->comp_q.front());
+                s->comp_q.pop_front();
+            }
         }
-        Request *r = c.req;
-        const uint64_t open = c.use << 1;  // the entry's use, not yet claimed
-        // A receiver polling r fulfils it itself (and may have received and
-        // reused it already: the claim word then reads otherwise); this
-        // thread stays out of the driver meanwhile and steps in only once no
-        // receiver is polling. (Checked every 20 us: a polling receiver
-        // claims its request within microseconds, and a tighter watch only
-        // costs it coherence misses.)
-        while (r->claim.load(std::memory_order_acquire) == open && r->waiting.load(std::memory_order_acquire))
-            std::this_thread::sleep_for(std::chrono::microseconds(20));
-        if (r->claim.load(std::memory_order_acquire) == open) {
+        for (auto it = mine.begin(); it != mine.end();) {
+            Request *r = it->req;
+            const uint64_t open = it->use << 1;  // the entry's use, not yet claimed
+            if (r->claim.load(std::memory_order_acquire) != open) {
+                it = mine.erase(it);
+                continue;
+            }
+            if (r->waiting.load(std::memory_order_acquire)) {
+                ++it;
+                continue;
+            }
             const ka_status st = cuda_status(cudaEventSynchronize(r->event));
-            if (try_claim(r, c.use)) finalize(s, r, st);
+            if (try_claim(r, it->use)) finalize(s, r, st);
+            it = mine.erase(it);
         }
+        if (s->stop.load() && s->inflight.load() <= 0) return;
     }
 }
 
@@ -1031,10 +1056,10 @@ ka_status ka_system_destroy(ka_system *h, int32_t force) {
     if (s->dispatcher.joinable()) s->dispatcher.join();
     // requests already launched finish normally; wait for the completer
     for (int i = 0; i < 200000 && s->inflight.load() > 0; ++i) {
-        s->comp_cv.notify_all();
+        kick_completer(s);
         std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
-    s->comp_cv.notify_all();
+    kick_completer(s);
     if (s->completer.joinable()) s->completer.join();
     cudaStreamSynchronize(s->stream);
     // Every handle of this system becomes stale (KA_E_STALE from then on):
@@ -1394,6 +1419,7 @@ ka_status ka_receive(ka_request_h *h, int64_t timeout_ns, ka_msg *out) {
         r->waiting.store(false, std::memory_order_release);
         if (!r->done.load(std::memory_order_acquire)) {
             r->blocked.store(true, std::memory_order_seq_cst);
+            kick_completer(s);  // it fulfils r from here
             std::unique_lock<std::mutex> l(r->mu);
             if (timeout_ns < 0) {
                 r->cv.wait(l, [&] { return r->done.load(); });
