@@ -147,6 +147,12 @@ __device__ __forceinline__ uint32_t compact_segment(uint32_t *seg, const PredDev
 // to dst (4-byte aligned): single entries up to dst's next 16-byte boundary,
 // then 16-byte stores, each assembled from two aligned 16-byte shared loads,
 // then the remaining single entries. cnt <= kSeg.
+// The 16-byte loops are kept rolled: a lane makes at most 4 trips, and in a
+// kernel with registers to spare the compiler unrolled them into predicated
+// stores that issue even when switched off. Those cost the held write-out
+// throughput (same array, same process: 273 -> 263 us at 50 % kept and 346
+// -> 324 us at 99 % in the five-stage shape, 352 -> 338 us at 99 % in the
+// four-stage one; the store instructions dropped from 578 K to 508 K).
 __device__ __forceinline__ void warp_copy_out(const uint32_t *src, uint32_t *dst, uint32_t cnt, int lane) {
     const uint32_t to16 = uint32_t((16u - (reinterpret_cast<uintptr_t>(dst) & 15u)) & 15u) >> 2;
     const uint32_t head = to16 < cnt ? to16 : cnt;
@@ -158,21 +164,25 @@ __device__ __forceinline__ void warp_copy_out(const uint32_t *src, uint32_t *dst
     // chunk i and the front of chunk i + 1 (index <= 127 since cnt <= 512).
     switch (head) {
     case 0:
+#pragma unroll 1
         for (uint32_t i = uint32_t(lane); i < body; i += 32) d4[i] = s4[i];
         break;
     case 1:
+#pragma unroll 1
         for (uint32_t i = uint32_t(lane); i < body; i += 32) {
             const uint4 x = s4[i], y = s4[i + 1];
             d4[i] = make_uint4(x.y, x.z, x.w, y.x);
         }
         break;
     case 2:
+#pragma unroll 1
         for (uint32_t i = uint32_t(lane); i < body; i += 32) {
             const uint4 x = s4[i], y = s4[i + 1];
             d4[i] = make_uint4(x.z, x.w, y.x, y.y);
         }
         break;
     default:
+#pragma unroll 1
         for (uint32_t i = uint32_t(lane); i < body; i += 32) {
             const uint4 x = s4[i], y = s4[i + 1];
             d4[i] = make_uint4(x.w, y.x, y.y, y.z);
