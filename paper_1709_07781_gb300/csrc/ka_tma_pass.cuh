@@ -580,6 +580,7 @@ __device__ __forceinline__ void tma_compact_pass(const TmaArgs &a) {
     const uint32_t mul = a.mul;
     uint32_t *const seg_base = stage_mem + w * kSeg;
     uint32_t *const spill_base = spill_mem + size_t(w) * NS * SPC;
+    const uint32_t lead_tiles = a.lead != 0u ? 1u : 0u;  // tile 0 starts before the input
     for (uint32_t j = 0; j < my_tiles + uint32_t(LAGS); ++j) {
         if (j >= uint32_t(LAG) && j - uint32_t(LAG) < my_tiles) {
             const uint32_t jp = j - uint32_t(LAG), k = jp & uint32_t(NS - 1);
@@ -608,13 +609,28 @@ __device__ __forceinline__ void tma_compact_pass(const TmaArgs &a) {
             const uint32_t tile = b + j * G, k = j & uint32_t(NS - 1);
             const int s = int(j % S);
             uint32_t *seg = seg_base + size_t(s) * T;
-            // entries [vlo, vhi) of this segment are input entries (64-bit
-            // position: the last tile's later segments can lie past 2^32 when
-            // T does not divide 2^32)
-            const uint64_t base = uint64_t(tile) * T + uint32_t(w) * kSeg;
-            const uint32_t vlo = base < a.lead ? a.lead - uint32_t(base) : 0u;
-            const uint32_t vhi = n > base ? uint32_t(min(n - base, uint64_t(kSeg))) : 0u;
-            tma_segment_ready(a, seg, &full_bar[s], (j / S) & 1u, tile < full_tiles, base, vlo, vhi, tile, lane);
+            // Entries [vlo, vhi) of this segment are input entries: all of them
+            // except in the first tile of an input with lead entries and in
+            // the ragged last tile, the only tiles that compute the bounds
+            // (64-bit position: the last tile's later segments can lie past
+            // 2^32 when T does not divide 2^32). The ragged tile is read with
+            // plain loads (zeros outside the input).
+            uint32_t vlo = 0u, vhi = uint32_t(kSeg);
+            const bool full_tile = tile < full_tiles;
+            if (!full_tile || tile < lead_tiles) {
+                const uint64_t base = uint64_t(tile) * T + uint32_t(w) * kSeg;
+                vlo = base < a.lead ? a.lead - uint32_t(base) : 0u;
+                vhi = n > base ? uint32_t(min(n - base, uint64_t(kSeg))) : 0u;
+                if (!full_tile) {
+                    const uint32_t *src = a.in + base;
+                    for (uint32_t e = uint32_t(lane); e < uint32_t(kSeg); e += 32)
+                        seg[e] = e >= vlo && e < vhi ? src[e] : 0u;
+                    __syncwarp();
+                }
+            }
+            if (full_tile && !mbar_wait(&full_bar[s], (j / S) & 1u) && lane == 0)
+                record_error(a.ws, kDevErrTimeout, tile);
+            const bool edge = vlo != 0u || vhi != uint32_t(kSeg);
             uint32_t v[ROWS][4], mk4[ROWS], packed = 0;
 #pragma unroll
             for (int r = 0; r < ROWS; ++r) {
@@ -635,7 +651,7 @@ __device__ __forceinline__ void tma_compact_pass(const TmaArgs &a) {
             for (int r = 0; r < ROWS; ++r) {
                 const uint32_t e0 = uint32_t(r * 128 + lane * 4);
                 uint32_t mk = mask4_of<PK>(a.pred, v[r][0], v[r][1], v[r][2], v[r][3]);
-                if (vlo != 0u || vhi != uint32_t(kSeg)) {
+                if (edge) {
                     const uint32_t skip = vlo > e0 ? min(vlo - e0, 4u) : 0u;
                     const uint32_t left = vhi > e0 ? vhi - e0 : 0u;
                     mk &= (0xFu << skip) & (left >= 4 ? 0xFu : ((1u << left) - 1u));
@@ -649,21 +665,44 @@ __device__ __forceinline__ void tma_compact_pass(const TmaArgs &a) {
             const uint32_t rows = __shfl_sync(kFull, incl, 31);
             const uint32_t total = (rows & 0xFFu) + ((rows >> 8) & 0xFFu) + ((rows >> 16) & 0xFFu) + (rows >> 24);
             const bool spilled = total <= uint32_t(SPC);
-            // shared-memory address of the destination (an explicit st.shared:
-            // a pointer chosen at run time would be stored through generically)
-            const uint32_t dst = smem_addr(spilled ? spill_base + k * SPC : seg);
-            __syncwarp();  // in place: every lane holds its entries before any is overwritten
-            uint32_t rowbase = 0;
-#pragma unroll
-            for (int r = 0; r < ROWS; ++r) {
-                uint32_t pos = rowbase + ((excl >> (8 * r)) & 0xFFu);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    if ((mk4[r] >> c) & 1u) st_shared_u32(dst + 4u * pos++, v[r][c]);
+            if (spilled) {
+                // At most kSpillCap entries for the whole warp: each lane
+                // stores only its own kept entries, in order, reading each
+                // back from the stage (as many trips as the busiest lane has
+                // kept entries; at low selectivity most lanes hold none, where
+                // the 16 predicated stores below cost every lane 16 slots).
+                // Entry r * 128 + 4 lane + c of the segment is bit 4 r + c of
+                // the lane's mask; its slot is the lane's first slot in row r
+                // (byte r of `first`: the rows before r plus the lanes before
+                // this one in row r; every count is at most 16, so no byte
+                // carries) plus its kept entries in row r already stored.
+                const uint32_t orig = mk4[0] | (mk4[1] << 4) | (mk4[2] << 8) | (mk4[3] << 12);
+                const uint32_t first = excl + rows * 0x01010100u;
+                uint32_t *const ring = spill_base + k * SPC;
+                const uint32_t *const mine = seg + uint32_t(lane) * 4u;
+                for (uint32_t m = orig; m != 0u; m &= m - 1u) {
+                    const uint32_t i = uint32_t(__ffs(int(m))) - 1u, r = i >> 2;
+                    const uint32_t pos = ((first >> (8u * r)) & 0xFFu) + __popc((orig ^ m) & (0xFu << (4u * r)));
+                    ring[pos] = mine[r * 128u + (i & 3u)] * mul;
                 }
-                rowbase += (rows >> (8 * r)) & 0xFFu;
+                __syncwarp();
+            } else {
+                // in place, at the front of the segment (an explicit st.shared
+                // to the segment's shared-memory address)
+                const uint32_t dst = smem_addr(seg);
+                __syncwarp();  // every lane holds its entries before any is overwritten
+                uint32_t rowbase = 0;
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    uint32_t pos = rowbase + ((excl >> (8 * r)) & 0xFFu);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        if ((mk4[r] >> c) & 1u) st_shared_u32(dst + 4u * pos++, v[r][c]);
+                    }
+                    rowbase += (rows >> (8 * r)) & 0xFFu;
+                }
+                __syncwarp();
             }
-            __syncwarp();
             if (lane == 0) {
                 s_wcnt[k][w] = total;
                 // the last segment counted publishes the tile aggregate at once
