@@ -517,7 +517,9 @@ typedef struct ka_serve_options {
                                     1: plain launches per request; 2: continuous
                                     batching with the tick's launches issued directly */
     uint32_t max_inflight;       /* admitted requests at most (0: 4096)              */
-    uint64_t budget_bytes;       /* admission budget (0: the system's)               */
+    uint64_t budget_bytes;       /* admission budget (0: the system's); the first
+                                    min(budget, 4 GiB) are reserved in the run's
+                                    memory pool before the loop starts           */
     double time_scale;           /* arrival_s multiplier (1.0 = real time)           */
     ka_tile tile;                /* batched kernel shape ({0,0}: autotuned/default)  */
     uint32_t flags;              /* KA_SERVE_* below (0: none)                       */

@@ -46,6 +46,7 @@ constexpr uint32_t kTickItems = 1024;        // requests per tick at most
 constexpr uint64_t kTickElems = 1ull << 28;  // input entries per tick at most
 constexpr int kTicks = 2;                    // ticks in flight at most
 constexpr int kDepth = 4;                    // stages per request at most
+constexpr uint64_t kPoolReserve = 4ull << 30;  // pool memory reserved at set-up (at most the budget)
 
 uint64_t bytes_for(uint32_t n) { return n ? (uint64_t(n) * 4 + 255) / 256 * 256 : 256; }
 
@@ -530,6 +531,19 @@ ka_status setup(Run &R, uint32_t max_n) {
     if (s != KA_OK) return s;
     uint64_t keep = ~0ull;  // keep freed memory in the pool for the next requests
     cudaMemPoolSetAttribute(R.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    // Reserve the pool's memory before the loop starts (allocated and freed
+    // here, kept by the release threshold above): growing a pool maps new
+    // memory, and inside the loop that took milliseconds (up to 62 ms once a
+    // backlog had built up), holding up the loop's other stream calls
+    // (frees, polls) meanwhile and so lengthening the backlog that caused it.
+    {
+        const uint64_t reserve = std::min<uint64_t>(R.budget, kPoolReserve);
+        void *p = nullptr;
+        if (reserve && cudaMallocFromPoolAsync(&p, reserve, R.pool, R.stream) == cudaSuccess)
+            cudaFreeAsync(p, R.stream);
+        else
+            cudaGetLastError();  // no reservation: the pool grows on demand
+    }
     if (R.mode != 1) {
         R.batch_tile = resolve_tile(KA_KERNEL_BATCH, kBatchTileKey, R.tile.block ? &R.tile : nullptr);
         R.grid_max = uint32_t(device_info().sm_count) * 8;

@@ -140,6 +140,57 @@ def varied_segments(seed, n, seg=512):
     return np.where(keep, u >> np.uint32(1), u | np.uint32(0x80000000)).astype(np.uint32)
 
 
+def patterned_segments(seed, n, seg=512):
+    """Entries rewritten so that `x < 2^31` keeps, in each `seg`-entry
+    segment, one of these sets (entry r * 128 + 4 l + c of a segment is row r,
+    lane l, column c of its warp's registers): none; the 16 entries of one
+    lane (lane 0 or lane 31: the most entries one lane of a spilled segment
+    can store, 16 trips); those 16 and one more (17: held); 16 entries spread
+    over random rows, lanes and columns; 15 consecutive entries across a row
+    boundary; 17 to 30 random entries; all of them."""
+    rng = np.random.default_rng(seed)
+    u = ki.uniform_u32(seed, n)
+    keep = np.zeros(n, dtype=bool)
+    lane_set = lambda l: np.array([r * 128 + 4 * l + c for r in range(4) for c in range(4)])
+    for b in range(0, n, seg):
+        m = min(seg, n - b)
+        kind = int(rng.integers(0, 8))
+        if kind == 0:
+            idx = np.array([], dtype=np.int64)
+        elif kind in (1, 2):
+            idx = lane_set(0 if kind == 1 else 31)
+        elif kind == 3:
+            idx = np.append(lane_set(int(rng.integers(0, 32))), int(rng.integers(0, seg)))
+        elif kind == 4:
+            idx = rng.choice(seg, size=16, replace=False)
+        elif kind == 5:
+            start = int(rng.choice([120, 250, 380, int(rng.integers(0, seg - 15))]))
+            idx = np.arange(start, start + 15)
+        elif kind == 6:
+            idx = rng.choice(seg, size=int(rng.integers(17, 31)), replace=False)
+        else:
+            idx = np.arange(seg)
+        idx = np.unique(idx)
+        keep[b + idx[idx < m]] = True
+    return np.where(keep, u >> np.uint32(1), u | np.uint32(0x80000000)).astype(np.uint32)
+
+
+@pytest.mark.parametrize("shape", TMA_SHAPES)
+@pytest.mark.parametrize("in_off", [0, 3])
+def test_tma_spill_patterns(ka, shape, in_off):
+    """The spilled segments' stores by set bit at their extremes: one lane
+    holding every kept entry, exactly 16 (spilled) against 17 (held), kept
+    runs across row boundaries, and spread entries, mixed with held and empty
+    segments in every tile; aligned and offset input."""
+    n = (1 << 22) + 777
+    x = patterned_segments(500 + in_off, n + in_off)
+    d = to_dev(x, pad=16)
+    y, ek = oracle.compact(x[in_off:], "lt", 1 << 31)
+    out, k = compact(ka, d[in_off:], n, "lt", 1 << 31, shape)
+    assert k == ek and np.array_equal(to_host(out, k), y)
+    assert np.all(to_host(out)[k:n + 16] == SENTINEL)
+
+
 @pytest.mark.parametrize("shape", TMA_SHAPES)
 @pytest.mark.parametrize("s", [0.001, 0.01, 0.02, 0.03, 0.04, 0.0625])
 def test_tma_low_selectivity(ka, shape, s):
